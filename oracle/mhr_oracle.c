@@ -1,0 +1,297 @@
+/*
+ * CPU oracle for exact three-hop top-K path search on a typed knowledge graph.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * definition the CUDA library is checked against.  It shares no code with the
+ * library; only tests, the package smoke check and the benchmark's CPU
+ * baseline leg may load it.  Build with -ffp-contract=off and without
+ * -Ofast / -ffast-math: the floating-point operation order below is the
+ * definition of the reference scores.
+ *
+ * What it computes (paper readings in brackets):
+ *   edge weight w(u,r,v), fp64, inputs converted exactly from the stored
+ *   float32 or bfloat16 values, j = 0..d-1 in order, no fused multiply-add:
+ *     TransE-L1 [Alg. 3 and Alg. 4: score = gamma - sum_j |agg[j] - e_t[j]|
+ *                with gamma = 1.0; Sec. 3.1: the TransE relation h + r - t;
+ *                Sec. 3.3: the aggregation of head and relation is h + r]
+ *        acc += fabs((e_u[j] + w_r[j]) - e_v[j]);   w = gamma - acc
+ *     DistMult (a bilinear form for the tensor-core variants; the paper
+ *               leaves the generic ComputeScore of Alg. 7 open)
+ *        acc += (e_u[j] * w_r[j]) * e_v[j];         w = acc
+ *   path s -r1-> u -r2-> v -r3-> t, simple: u not in {s,t}, v not in {s,t,u}
+ *     [Alg. 7: a neighbour already on the path is skipped and reaching the
+ *      target ends the path]
+ *   path score S = (w1 + w2) + w3   (sum of the three edge weights)
+ *   result: the K best paths in the total order
+ *     score descending, then (u, r1, v, r2, r3) ascending,
+ *   kept with a bounded heap of the K best [Sec. 3.3: per-thread k-heaps that
+ *   keep only the K highest scores; the "MaxHeap" of Alg. 3/4 is read as the
+ *   structure that keeps the K highest scores, evicting the lowest].
+ *
+ * Parity pins (tests/): hand-derived examples with dyadic embeddings, closed
+ * forms (zero embeddings), the exact rational edge weight within the fp64
+ * rounding bound, an independent meet-in-the-middle route in pure Python,
+ * brute-force invariants (K = all equals the full sorted enumeration, prefix
+ * consistency in K).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef __FAST_MATH__
+#error "the oracle must be built without -ffast-math"
+#endif
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    double score;
+    uint32_t u, v;
+    uint16_t r1, r2, r3, pad;
+} oracle_path;                      /* 24 bytes, same layout as the library's */
+
+typedef struct {
+    int64_t deg_s;   /* out-degree of s */
+    int64_t deg_t;   /* in-degree of t */
+    int64_t n_u;     /* distinct u in N_out(s) \ {s,t} */
+    int64_t n_v;     /* distinct v in N_in(t) \ {s,t} */
+    int64_t s_f;     /* sum of out-degrees over those u */
+    int64_t s_b;     /* sum of in-degrees over those v */
+    int64_t hits;    /* middle edges (u,r2,v) with u, v as above and v != u */
+    int64_t paths;   /* number of simple s->t three-hop paths */
+} oracle_stats;
+
+enum { ORACLE_OK = 0, ORACLE_EINVAL = 1, ORACLE_ENOMEM = 2 };
+enum { ORACLE_TRANSE_L1 = 0, ORACLE_DISTMULT = 1 };
+enum { ORACLE_F32 = 0, ORACLE_BF16 = 1 };
+
+/* ------------------------------------------------------------------------ */
+static double load_elem(const void* tab, int dtype, int64_t row, int d, int j) {
+    if (dtype == ORACLE_F32) {
+        return (double)((const float*)tab)[row * (int64_t)d + j];
+    } else {
+        uint32_t bits = (uint32_t)((const uint16_t*)tab)[row * (int64_t)d + j] << 16;
+        float f;
+        memcpy(&f, &bits, sizeof f);
+        return (double)f;
+    }
+}
+
+double oracle_edge_weight(const void* vemb, const void* remb, int dtype, int d, int fn,
+                          double gamma, uint32_t u, uint32_t r, uint32_t v) {
+    double acc = 0.0;
+    if (fn == ORACLE_TRANSE_L1) {
+        for (int j = 0; j < d; ++j) {
+            double a = load_elem(vemb, dtype, u, d, j);
+            double b = load_elem(remb, dtype, r, d, j);
+            double c = load_elem(vemb, dtype, v, d, j);
+            double h_plus_r = a + b;
+            double diff = h_plus_r - c;
+            acc = acc + fabs(diff);
+        }
+        return gamma - acc;
+    } else {
+        for (int j = 0; j < d; ++j) {
+            double a = load_elem(vemb, dtype, u, d, j);
+            double b = load_elem(remb, dtype, r, d, j);
+            double c = load_elem(vemb, dtype, v, d, j);
+            double ab = a * b;
+            double abc = ab * c;
+            acc = acc + abc;
+        }
+        return acc;
+    }
+}
+
+int oracle_edge_weights(const void* vemb, const void* remb, int dtype, int d, int fn, double gamma,
+                        const uint32_t* src, const uint16_t* rel, const uint32_t* dst, int64_t m,
+                        double* out) {
+    for (int64_t i = 0; i < m; ++i)
+        out[i] = oracle_edge_weight(vemb, remb, dtype, d, fn, gamma, src[i], rel[i], dst[i]);
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 1 if p ranks strictly before q in the result order */
+static int ranks_before(const oracle_path* p, const oracle_path* q) {
+    if (p->score != q->score) return p->score > q->score;
+    if (p->u != q->u) return p->u < q->u;
+    if (p->r1 != q->r1) return p->r1 < q->r1;
+    if (p->v != q->v) return p->v < q->v;
+    if (p->r2 != q->r2) return p->r2 < q->r2;
+    return p->r3 < q->r3;
+}
+
+static int cmp_rank(const void* a, const void* b) {
+    const oracle_path* p = (const oracle_path*)a;
+    const oracle_path* q = (const oracle_path*)b;
+    if (ranks_before(p, q)) return -1;
+    if (ranks_before(q, p)) return 1;
+    return 0;
+}
+
+/* Bounded heap of the K best paths; the root is the worst kept path. */
+typedef struct {
+    oracle_path* a;
+    int64_t size, cap;
+} khe;
+
+static void khe_swap(oracle_path* x, oracle_path* y) {
+    oracle_path tmp = *x;
+    *x = *y;
+    *y = tmp;
+}
+
+static void khe_push(khe* h, const oracle_path* p) {
+    if (h->size < h->cap) {
+        int64_t i = h->size++;
+        h->a[i] = *p;
+        while (i > 0) {                       /* sift up: parent must be worse */
+            int64_t par = (i - 1) / 2;
+            if (ranks_before(&h->a[par], &h->a[i])) {
+                khe_swap(&h->a[par], &h->a[i]);
+                i = par;
+            } else {
+                break;
+            }
+        }
+        return;
+    }
+    if (!ranks_before(p, &h->a[0])) return;   /* not better than the worst kept */
+    h->a[0] = *p;
+    int64_t i = 0;
+    for (;;) {                                /* sift down: move the worst up */
+        int64_t l = 2 * i + 1, r = l + 1, w = i;
+        if (l < h->size && ranks_before(&h->a[w], &h->a[l])) w = l;
+        if (r < h->size && ranks_before(&h->a[w], &h->a[r])) w = r;
+        if (w == i) break;
+        khe_swap(&h->a[w], &h->a[i]);
+        i = w;
+    }
+}
+
+/* first index in cols[lo, hi) whose value is >= key (rows are sorted by col) */
+static int64_t lower_bound_u32(const uint32_t* cols, int64_t lo, int64_t hi, uint32_t key) {
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (cols[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+/*
+ * Brute force: every out-edge (s,r1,u), every out-edge (u,r2,v) of u, every
+ * edge (v,r3,t) found by binary search in the sorted row of v.
+ */
+int oracle_topk_paths(const int64_t* offsets, const uint32_t* cols, const uint16_t* rels, int64_t n,
+                      const void* vemb, const void* remb, int dtype, int d, int fn, double gamma,
+                      uint32_t s, uint32_t t, int64_t K, oracle_path* out, int64_t* n_out,
+                      int64_t* hits_out, int64_t* paths_out) {
+    if ((int64_t)s >= n || (int64_t)t >= n || s == t || K <= 0) return ORACLE_EINVAL;
+    khe h;
+    h.a = (oracle_path*)malloc(sizeof(oracle_path) * (size_t)K);
+    if (!h.a) return ORACLE_ENOMEM;
+    h.size = 0;
+    h.cap = K;
+    int64_t hits = 0, paths = 0;
+    for (int64_t i = offsets[s]; i < offsets[s + 1]; ++i) {
+        uint32_t u = cols[i];
+        uint16_t r1 = rels[i];
+        if (u == s || u == t) continue;
+        int first_edge_to_u = (i == offsets[s] || cols[i - 1] != u);   /* rows sorted by col */
+        double w1 = oracle_edge_weight(vemb, remb, dtype, d, fn, gamma, s, r1, u);
+        for (int64_t j = offsets[u]; j < offsets[u + 1]; ++j) {
+            uint32_t v = cols[j];
+            uint16_t r2 = rels[j];
+            if (v == s || v == t || v == u) continue;
+            int64_t k = lower_bound_u32(cols, offsets[v], offsets[v + 1], t);
+            if (k >= offsets[v + 1] || cols[k] != t) continue;
+            if (first_edge_to_u) ++hits;
+            double w2 = oracle_edge_weight(vemb, remb, dtype, d, fn, gamma, u, r2, v);
+            for (; k < offsets[v + 1] && cols[k] == t; ++k) {
+                uint16_t r3 = rels[k];
+                double w3 = oracle_edge_weight(vemb, remb, dtype, d, fn, gamma, v, r3, t);
+                oracle_path p;
+                p.score = (w1 + w2) + w3;
+                p.u = u;
+                p.v = v;
+                p.r1 = r1;
+                p.r2 = r2;
+                p.r3 = r3;
+                p.pad = 0;
+                khe_push(&h, &p);
+                ++paths;
+            }
+        }
+    }
+    qsort(h.a, (size_t)h.size, sizeof(oracle_path), cmp_rank);
+    memcpy(out, h.a, sizeof(oracle_path) * (size_t)h.size);
+    *n_out = h.size;
+    if (hits_out) *hits_out = hits;
+    if (paths_out) *paths_out = paths;
+    free(h.a);
+    return ORACLE_OK;
+}
+
+/* Many queries, independent, in parallel over queries (OpenMP when built with it). */
+int oracle_topk_paths_batch(const int64_t* offsets, const uint32_t* cols, const uint16_t* rels,
+                            int64_t n, const void* vemb, const void* remb, int dtype, int d, int fn,
+                            double gamma, int64_t nq, const uint32_t* S, const uint32_t* T,
+                            int64_t K, oracle_path* out, int64_t* n_out, int32_t* status) {
+    int any = ORACLE_OK;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < nq; ++q) {
+        int st = oracle_topk_paths(offsets, cols, rels, n, vemb, remb, dtype, d, fn, gamma, S[q],
+                                   T[q], K, out + q * K, &n_out[q], NULL, NULL);
+        status[q] = st;
+        if (st != ORACLE_OK) {
+#pragma omp atomic write
+            any = st;
+        }
+    }
+    return any;
+}
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/*
+ * Per-query frontier statistics (the counts the library's byte model uses).
+ * In-degrees are counted from the edge array directly.
+ */
+int oracle_query_stats(const int64_t* offsets, const uint32_t* cols, int64_t n, uint32_t s,
+                       uint32_t t, oracle_stats* st) {
+    if ((int64_t)s >= n || (int64_t)t >= n || s == t) return ORACLE_EINVAL;
+    int64_t E = offsets[n];
+    int64_t* indeg = (int64_t*)calloc((size_t)n, sizeof(int64_t));
+    if (!indeg) return ORACLE_ENOMEM;
+    for (int64_t e = 0; e < E; ++e) indeg[cols[e]]++;
+    memset(st, 0, sizeof *st);
+    st->deg_s = offsets[s + 1] - offsets[s];
+    st->deg_t = indeg[t];
+    for (int64_t i = offsets[s]; i < offsets[s + 1]; ++i) {
+        uint32_t u = cols[i];
+        if (u == s || u == t) continue;
+        if (i > offsets[s] && cols[i - 1] == u) continue;   /* count each u once */
+        st->n_u++;
+        st->s_f += offsets[u + 1] - offsets[u];
+    }
+    for (int64_t v = 0; v < n; ++v) {
+        if (v == s || v == t) continue;
+        int64_t k = lower_bound_u32(cols, offsets[v], offsets[v + 1], t);
+        if (k < offsets[v + 1] && cols[k] == t) {
+            st->n_v++;
+            st->s_b += indeg[v];
+        }
+    }
+    free(indeg);
+    return ORACLE_OK;
+}
