@@ -1,0 +1,178 @@
+/*
+ * mhr.h - C ABI of the GB300 exact three-hop top-K path-search library
+ * (libmhr.so, sm_103a).
+ *
+ * Problem (Sec. 3.1; Sec. 5, Alg. 6 and Alg. 7): given a typed knowledge graph
+ * as (h, r, t) triples, an entity embedding table and a relation embedding
+ * table, return the K best paths s -r1-> u -r2-> v -r3-> t.
+ *   - Edge weight (Alg. 3, Alg. 4): TransE-L1  w = gamma - sum_j |e_u + w_r - e_v|_j
+ *     with gamma = 1.0 in the paper, or DistMult w = sum_j e_u[j] w_r[j] e_v[j]
+ *     (a bilinear choice for the generic ComputeScore of Alg. 7, which the
+ *     paper leaves open).
+ *   - Paths are simple: u not in {s, t}, v not in {s, t, u} (Alg. 7 skips a
+ *     neighbour already on the path; reaching t ends a path).
+ *   - Path score = sum of its three edge weights.
+ *   - Result order: score descending, then (u, r1, v, r2, r3) ascending.  This
+ *     is a total order, so the result is unique.
+ * Every result is exact: candidates are screened in fp32 with a proven error
+ * bound and the boundary candidates are rescored in fp64 in a fixed operation
+ * order, so scores and order equal an fp64 brute-force enumeration
+ * (j = 0..d-1 in order, no fused multiply-add).
+ *
+ * Conventions for every entry point:
+ *   - Status codes are returned, never raised; mhr_last_error() gives a
+ *     thread-local message for the last non-OK status of the calling thread.
+ *   - The caller owns every buffer it passes.  mhr_graph_load copies what it
+ *     needs; the graph handle owns its device copy until mhr_graph_free.
+ *   - cuda_stream is a cudaStream_t (NULL = the legacy default stream).
+ *   - The device is the one current on the calling thread when the graph is
+ *     loaded; later calls on that graph must use the same device.
+ */
+#ifndef MHR_H
+#define MHR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MHR_OK = 0,
+    MHR_EINVAL = 1,   /* invalid argument or invalid graph */
+    MHR_ENOMEM = 2,   /* host or device allocation failed */
+    MHR_ECUDA = 3,    /* a CUDA call or kernel failed */
+    MHR_ETIMEOUT = 4, /* a bounded device wait gave up */
+    MHR_ERANGE = 5    /* K or a size beyond a documented limit */
+} mhr_status;
+
+typedef enum {
+    MHR_SCORE_TRANSE_L1 = 0, /* gamma - ||e_u + w_r - e_v||_1 (Alg. 3, Alg. 4) */
+    MHR_SCORE_DISTMULT = 1   /* <e_u * w_r, e_v> */
+} mhr_score_fn;
+
+typedef enum { MHR_F32 = 0, MHR_BF16 = 1 } mhr_dtype;
+typedef enum { MHR_MEM_HOST = 0, MHR_MEM_DEVICE = 1 } mhr_mem;
+
+/* Largest K a query accepts; larger K returns MHR_ERANGE. */
+#define MHR_K_MAX 1024
+
+typedef struct mhr_graph mhr_graph; /* opaque; owned by the library */
+
+/*
+ * Graph description (Sec. 3.1: edge list, entity embeddings, relation
+ * embeddings).  All arrays are borrowed for the duration of mhr_graph_load.
+ *   offsets     int64[n_vertices + 1]  CSR row starts by source vertex;
+ *               offsets[0] = 0, non-decreasing, offsets[n] = n_edges
+ *   cols        uint32[n_edges]        destination of each edge
+ *   rels        uint16[n_edges]        relation id of each edge, < n_relations
+ *   vtypes      uint8[n_vertices]      vertex type ids (may be NULL: all 0)
+ *   vertex_emb  [n_vertices x dim]     row-major, float32 or bfloat16 bits
+ *   rel_emb     [n_relations x dim]    row-major, same dtype
+ * Each row must be sorted by (col, rel) with no repeated (col, rel) and no
+ * self loop; every embedding value must be finite; n_vertices, n_edges < 2^32.
+ * mem tells whether the arrays are host or device pointers.
+ */
+typedef struct {
+    int64_t n_vertices;
+    int64_t n_edges;
+    int32_t n_relations;
+    int32_t n_vtypes;
+    int32_t dim;
+    int32_t reserved0;
+    const int64_t* offsets;
+    const uint32_t* cols;
+    const uint16_t* rels;
+    const uint8_t* vtypes;
+    const void* vertex_emb;
+    const void* rel_emb;
+    mhr_dtype emb_dtype;
+    mhr_mem mem;
+    mhr_score_fn score_fn;
+    int32_t reserved1;
+    double gamma; /* TransE margin; the paper uses 1.0 */
+} mhr_graph_desc;
+
+/* One result path s -r1-> u -r2-> v -r3-> t; score is the fp64 sum of the
+ * three edge weights.  24 bytes. */
+typedef struct {
+    double score;
+    uint32_t u, v;
+    uint16_t r1, r2, r3, pad;
+} mhr_path;
+
+/* Query options; a NULL pointer means all defaults (zeros). */
+typedef struct {
+    int32_t chunk;       /* edges per work item of the middle join; 0 = autotuned/default */
+    int32_t order;       /* 0 = natural order of intermediate vertices */
+    int32_t prune;       /* 0 = no bound pruning */
+    int32_t reserved[5];
+} mhr_query_opts;
+
+/* Work counters of the last call (optional output). */
+typedef struct {
+    int64_t edges_scanned; /* middle-join CSR entries streamed */
+    int64_t hits;          /* middle edges that joined both frontiers */
+    int64_t candidates;    /* fp32 candidates kept for the final merge */
+    int64_t rescored;      /* candidates rescored in fp64 */
+    int64_t pruned_edges;  /* middle edges skipped by provable bounds */
+    int64_t dense_queries; /* queries resolved by the exact (tie-heavy) path */
+    double ms;             /* wall time of the call (synchronous calls only) */
+} mhr_stats;
+
+/*
+ * Upload a graph and build its device indexes: the reverse CSR (in-edges of
+ * each vertex, sorted by (source, relation)) and the norms behind the fp32
+ * error bound.  Validates the description (MHR_EINVAL with a message on any
+ * violation).  Synchronous; *out is NULL on failure.
+ */
+mhr_status mhr_graph_load(const mhr_graph_desc* desc, mhr_graph** out, void* cuda_stream);
+
+/* Release the device copy.  NULL is accepted. */
+mhr_status mhr_graph_free(mhr_graph* g);
+
+/*
+ * Edge weights w(src[i], rel[i], dst[i]) for i < n (Alg. 3, Alg. 4 score form).
+ *   precision 0: float32 output, fp32 arithmetic (the screening arithmetic)
+ *   precision 2: float64 output, the canonical fp64 operation order
+ * src == NULL (then rel and dst must be NULL too): all edges in CSR order and
+ * n must equal n_edges.  mem applies to src, rel, dst and out.  Asynchronous
+ * on cuda_stream for device memory, synchronous for host memory.
+ */
+mhr_status mhr_edge_scores(const mhr_graph* g, const uint32_t* src, const uint16_t* rel,
+                           const uint32_t* dst, int64_t n, int32_t precision, void* out,
+                           mhr_mem mem, void* cuda_stream);
+
+/*
+ * One query, synchronous.  out: host array of K paths; *n_out = number
+ * written (< K when fewer paths exist).  s, t < n_vertices, s != t,
+ * 1 <= K <= MHR_K_MAX (else MHR_EINVAL / MHR_ERANGE).
+ */
+mhr_status mhr_topk_paths(const mhr_graph* g, uint32_t s, uint32_t t, int32_t K, mhr_path* out,
+                          int32_t* n_out, const mhr_query_opts* opts, mhr_stats* stats);
+
+/*
+ * nq independent queries (s[i], t[i]) in one batched launch sequence that is
+ * captured once into a CUDA graph and replayed.  out: nq*K paths (query i at
+ * out[i*K]); n_out[i] = paths written for query i, or -1 when (s[i], t[i]) is
+ * invalid (out of range or s == t).  mem applies to s, t, out and n_out.
+ * Host memory: synchronous.  Device memory: asynchronous on cuda_stream
+ * (the query sizes are read back once, a short synchronisation).  stats, if
+ * not NULL, forces a synchronisation at the end.
+ */
+mhr_status mhr_topk_paths_batched(const mhr_graph* g, int32_t nq, const uint32_t* s,
+                                  const uint32_t* t, int32_t K, mhr_path* out, int32_t* n_out,
+                                  mhr_mem mem, const mhr_query_opts* opts, mhr_stats* stats,
+                                  void* cuda_stream);
+
+/* Thread-local description of the last non-OK status ("" if none). */
+const char* mhr_last_error(void);
+
+/* Library version string. */
+const char* mhr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MHR_H */

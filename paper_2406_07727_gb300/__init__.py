@@ -1,0 +1,38 @@
+"""GB300-native exact three-hop top-K path search (libmhr.so, sm_103a).
+
+The compute path is the CUDA library behind the C ABI in include/mhr.h; this
+package only marshals arguments to it (see _mhr.py) and compiles it
+(build.py).  Importing the package loads the library and fails loudly when it
+cannot be built or loaded: there is no CPU fallback.
+"""
+
+from ._mhr import (  # noqa: F401
+    EXPORTS,
+    Graph,
+    MhrError,
+    PATH_DTYPE,
+    MHR_K_MAX,
+    MHR_OK,
+    MHR_EINVAL,
+    MHR_ENOMEM,
+    MHR_ECUDA,
+    MHR_ETIMEOUT,
+    MHR_ERANGE,
+    MHR_SCORE_TRANSE_L1,
+    MHR_SCORE_DISTMULT,
+    QueryOpts,
+    Stats,
+    lib_path,
+    load_kg,
+    load_library,
+    mhr_edge_scores,
+    mhr_graph_free,
+    mhr_graph_load,
+    mhr_last_error,
+    mhr_topk_paths,
+    mhr_topk_paths_batched,
+    mhr_version,
+    paths_from_device,
+)
+
+load_library()

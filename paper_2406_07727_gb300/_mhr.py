@@ -1,0 +1,322 @@
+"""ctypes binding of libmhr.so: argument marshalling only.
+
+Every entry point has the C name and forwards to the C ABI (include/mhr.h);
+there is no Python or CPU fallback for any computation.  Arrays may be NumPy
+arrays (host memory) or torch CUDA tensors (device memory); the memory kind is
+passed to the library, which does the copies it needs.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+MHR_OK, MHR_EINVAL, MHR_ENOMEM, MHR_ECUDA, MHR_ETIMEOUT, MHR_ERANGE = range(6)
+MHR_SCORE_TRANSE_L1, MHR_SCORE_DISTMULT = 0, 1
+MHR_F32, MHR_BF16 = 0, 1
+MHR_MEM_HOST, MHR_MEM_DEVICE = 0, 1
+MHR_K_MAX = 1024
+
+STATUS_NAMES = {0: "MHR_OK", 1: "MHR_EINVAL", 2: "MHR_ENOMEM", 3: "MHR_ECUDA", 4: "MHR_ETIMEOUT",
+                5: "MHR_ERANGE"}
+SCORE_FNS = {"transe": MHR_SCORE_TRANSE_L1, "transe_l1": MHR_SCORE_TRANSE_L1,
+             "distmult": MHR_SCORE_DISTMULT}
+
+PATH_DTYPE = np.dtype([("score", "<f8"), ("u", "<u4"), ("v", "<u4"),
+                       ("r1", "<u2"), ("r2", "<u2"), ("r3", "<u2"), ("pad", "<u2")])
+assert PATH_DTYPE.itemsize == 24
+
+
+class MhrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("n_edges", ctypes.c_int64),
+                ("n_relations", ctypes.c_int32), ("n_vtypes", ctypes.c_int32),
+                ("dim", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("offsets", ctypes.c_void_p), ("cols", ctypes.c_void_p), ("rels", ctypes.c_void_p),
+                ("vtypes", ctypes.c_void_p), ("vertex_emb", ctypes.c_void_p),
+                ("rel_emb", ctypes.c_void_p), ("emb_dtype", ctypes.c_int), ("mem", ctypes.c_int),
+                ("score_fn", ctypes.c_int), ("reserved1", ctypes.c_int32),
+                ("gamma", ctypes.c_double)]
+
+
+class QueryOpts(ctypes.Structure):
+    _fields_ = [("chunk", ctypes.c_int32), ("order", ctypes.c_int32), ("prune", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("edges_scanned", ctypes.c_int64), ("hits", ctypes.c_int64),
+                ("candidates", ctypes.c_int64), ("rescored", ctypes.c_int64),
+                ("pruned_edges", ctypes.c_int64), ("dense_queries", ctypes.c_int64),
+                ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ("mhr_graph_load", "mhr_graph_free", "mhr_edge_scores", "mhr_topk_paths",
+           "mhr_topk_paths_batched", "mhr_last_error", "mhr_version")
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libmhr.so (building it with nvcc when missing); raises if neither works."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"libmhr.so not found at {path}; run paper_2406_07727_gb300/build.py")
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i32, i64 = ctypes.c_int32, ctypes.c_int64
+        lib.mhr_graph_load.restype = ctypes.c_int
+        lib.mhr_graph_load.argtypes = [ctypes.POINTER(GraphDesc), ctypes.POINTER(P), P]
+        lib.mhr_graph_free.restype = ctypes.c_int
+        lib.mhr_graph_free.argtypes = [P]
+        lib.mhr_edge_scores.restype = ctypes.c_int
+        lib.mhr_edge_scores.argtypes = [P, P, P, P, i64, i32, P, ctypes.c_int, P]
+        lib.mhr_topk_paths.restype = ctypes.c_int
+        lib.mhr_topk_paths.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, i32, P, P,
+                                       ctypes.POINTER(QueryOpts), ctypes.POINTER(Stats)]
+        lib.mhr_topk_paths_batched.restype = ctypes.c_int
+        lib.mhr_topk_paths_batched.argtypes = [P, i32, P, P, i32, P, P, ctypes.c_int,
+                                               ctypes.POINTER(QueryOpts), ctypes.POINTER(Stats), P]
+        lib.mhr_last_error.restype = ctypes.c_char_p
+        lib.mhr_last_error.argtypes = []
+        lib.mhr_version.restype = ctypes.c_char_p
+        lib.mhr_version.argtypes = []
+        _lib = lib
+        return lib
+
+
+def mhr_last_error() -> str:
+    return load_library().mhr_last_error().decode()
+
+
+def mhr_version() -> str:
+    return load_library().mhr_version().decode()
+
+
+def _check(rc: int):
+    if rc != MHR_OK:
+        raise MhrError(rc, mhr_last_error())
+
+
+# --------------------------------------------------------------------------- marshalling
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def _mem_of(*arrays) -> int:
+    kinds = {MHR_MEM_DEVICE if _is_torch_cuda(a) else MHR_MEM_HOST for a in arrays if a is not None}
+    if len(kinds) > 1:
+        raise ValueError("mixing host and device arrays in one call")
+    return kinds.pop() if kinds else MHR_MEM_HOST
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch_cuda(a):
+        if not a.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host arrays must be C-contiguous numpy arrays")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _opts(opts) -> Optional[QueryOpts]:
+    if opts is None:
+        return None
+    if isinstance(opts, QueryOpts):
+        return opts
+    o = QueryOpts()
+    for k, v in dict(opts).items():
+        setattr(o, k, int(v))
+    return o
+
+
+# --------------------------------------------------------------------------- API
+class Graph:
+    """Owns one mhr_graph handle (freed by close() or garbage collection)."""
+
+    def __init__(self, handle: int, n: int, E: int, R: int, d: int, score_fn: int):
+        self._h = handle
+        self.n, self.E, self.R, self.d = n, E, R, d
+        self.score_fn = score_fn
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("graph is closed")
+        return ctypes.c_void_p(self._h)
+
+    def close(self):
+        if self._h:
+            load_library().mhr_graph_free(ctypes.c_void_p(self._h))
+            self._h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mhr_graph_load(offsets, cols, rels, vertex_emb, rel_emb, n_relations: int, *, vtypes=None,
+                   n_vtypes: int = 1, score_fn="transe", gamma: float = 1.0, emb_dtype="f32",
+                   stream=None) -> Graph:
+    """Upload a graph (numpy host arrays or torch CUDA tensors)."""
+    lib = load_library()
+    mem = _mem_of(offsets, cols, rels, vertex_emb, rel_emb, vtypes)
+    if mem == MHR_MEM_HOST:
+        offsets = _host(offsets, np.int64)
+        cols = _host(cols, np.uint32)
+        rels = _host(rels, np.uint16)
+        dt = np.float32 if emb_dtype == "f32" else np.uint16
+        vertex_emb = _host(vertex_emb, dt)
+        rel_emb = _host(rel_emb, dt)
+        if vtypes is not None:
+            vtypes = _host(vtypes, np.uint8)
+    n = int(offsets.shape[0]) - 1
+    E = int(cols.shape[0])
+    d = int(vertex_emb.shape[1])
+    desc = GraphDesc()
+    desc.n_vertices, desc.n_edges = n, E
+    desc.n_relations, desc.n_vtypes, desc.dim = int(n_relations), int(n_vtypes), d
+    desc.offsets, desc.cols, desc.rels = _ptr(offsets), _ptr(cols), _ptr(rels)
+    desc.vtypes = _ptr(vtypes)
+    desc.vertex_emb, desc.rel_emb = _ptr(vertex_emb), _ptr(rel_emb)
+    desc.emb_dtype = MHR_F32 if emb_dtype == "f32" else MHR_BF16
+    desc.mem = mem
+    desc.score_fn = SCORE_FNS[score_fn] if isinstance(score_fn, str) else int(score_fn)
+    desc.gamma = float(gamma)
+    h = ctypes.c_void_p()
+    _check(lib.mhr_graph_load(ctypes.byref(desc), ctypes.byref(h), _stream_ptr(stream)))
+    return Graph(h.value, n, E, int(n_relations), d, desc.score_fn)
+
+
+def mhr_graph_free(g: Graph):
+    g.close()
+
+
+def mhr_edge_scores(g: Graph, src=None, rel=None, dst=None, precision: int = 0, out=None,
+                    stream=None):
+    """Edge weights; precision 0 -> float32 (fp32 arithmetic), 2 -> float64
+    (canonical fp64 order).  src is None: all edges in CSR order."""
+    lib = load_library()
+    mem = _mem_of(src, rel, dst, out)
+    n = g.E if src is None else int(src.shape[0])
+    if mem == MHR_MEM_HOST:
+        if src is not None:
+            src, rel, dst = _host(src, np.uint32), _host(rel, np.uint16), _host(dst, np.uint32)
+        if out is None:
+            out = np.empty(n, dtype=np.float32 if precision == 0 else np.float64)
+    elif out is None:
+        import torch
+        out = torch.empty(n, dtype=torch.float32 if precision == 0 else torch.float64,
+                          device=src.device)
+    _check(lib.mhr_edge_scores(g.handle, _ptr(src), _ptr(rel), _ptr(dst), n, int(precision),
+                               _ptr(out), mem, _stream_ptr(stream)))
+    return out
+
+
+def mhr_topk_paths(g: Graph, s: int, t: int, K: int, opts=None, with_stats: bool = False):
+    """One query, synchronous; returns a structured array of PATH_DTYPE."""
+    lib = load_library()
+    out = np.zeros(max(int(K), 1), dtype=PATH_DTYPE)
+    n_out = ctypes.c_int32(0)
+    st = Stats()
+    o = _opts(opts)
+    rc = lib.mhr_topk_paths(g.handle, ctypes.c_uint32(int(s) & 0xFFFFFFFF),
+                            ctypes.c_uint32(int(t) & 0xFFFFFFFF), int(K), _ptr(out),
+                            ctypes.byref(n_out), ctypes.byref(o) if o is not None else None,
+                            ctypes.byref(st))
+    _check(rc)
+    res = out[: n_out.value].copy()
+    return (res, st.as_dict()) if with_stats else res
+
+
+def mhr_topk_paths_batched(g: Graph, S, T, K: int, out=None, n_out=None, opts=None, stream=None,
+                           with_stats: bool = False):
+    """nq queries.  Host arrays in -> host arrays out (synchronous); device
+    tensors in -> device tensors out (asynchronous on `stream`).  Returns
+    (paths [nq, K] of PATH_DTYPE or a uint8 tensor [nq, K*24], n_out [nq])."""
+    lib = load_library()
+    mem = _mem_of(S, T, out, n_out)
+    nq = int(S.shape[0])
+    if mem == MHR_MEM_HOST:
+        S, T = _host(S, np.uint32), _host(T, np.uint32)
+        if out is None:
+            out = np.zeros((nq, int(K)), dtype=PATH_DTYPE)
+        if n_out is None:
+            n_out = np.zeros(nq, dtype=np.int32)
+    else:
+        import torch
+        if out is None:
+            out = torch.empty((nq, int(K) * PATH_DTYPE.itemsize), dtype=torch.uint8, device=S.device)
+        if n_out is None:
+            n_out = torch.empty(nq, dtype=torch.int32, device=S.device)
+    st = Stats()
+    o = _opts(opts)
+    rc = lib.mhr_topk_paths_batched(g.handle, nq, _ptr(S), _ptr(T), int(K), _ptr(out), _ptr(n_out),
+                                    mem, ctypes.byref(o) if o is not None else None,
+                                    ctypes.byref(st) if with_stats else None, _stream_ptr(stream))
+    _check(rc)
+    if with_stats:
+        return out, n_out, st.as_dict()
+    return out, n_out
+
+
+def paths_from_device(buf, K: int) -> np.ndarray:
+    """uint8 device/host buffer [nq, K*24] -> structured numpy array [nq, K]."""
+    if hasattr(buf, "cpu"):
+        buf = buf.cpu().numpy()
+    buf = np.ascontiguousarray(buf)
+    return buf.view(PATH_DTYPE).reshape(buf.shape[0], K)
+
+
+def load_kg(kg, score_fn="transe", gamma=1.0, device: bool = False, stream=None) -> Graph:
+    """Convenience: upload a synth.KG-like object (fields offsets, cols, rels,
+    vtypes, vemb, remb, dtype, R, n_types)."""
+    arrays = [kg.offsets, kg.cols, kg.rels, kg.vemb, kg.remb, kg.vtypes]
+    if device:
+        import torch
+        arrays = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrays]
+    off, cols, rels, vemb, remb, vt = arrays
+    return mhr_graph_load(off, cols, rels, vemb, remb, kg.R, vtypes=vt, n_vtypes=kg.n_types,
+                          score_fn=score_fn, gamma=gamma, emb_dtype=kg.dtype, stream=stream)

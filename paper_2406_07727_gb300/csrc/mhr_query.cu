@@ -1,0 +1,1386 @@
+// Batched exact three-hop top-K path search (the hot path).
+//
+// For each query (s, t) every simple path s -r1-> u -r2-> v -r3-> t is scored
+// as w(s,r1,u) + w(u,r2,v) + w(v,r3,t) and the K best are returned in the
+// order score descending, (u, r1, v, r2, r3) ascending.  The paper's CPU
+// design (Sec. 3.3, Alg. 2-4; Sec. 5, Alg. 6-7) keeps thread-private k-heaps
+// and merges them with a barrier tree; here the same exact result comes from
+// a meet-in-the-middle join sized for one GB300:
+//
+//   expand   hop-1 row of s and hop-3 (reverse) row of t, fp32 weights,
+//            distinct frontier vertices with their best weight       (k_expand, k_lists)
+//   plan     per query: S_f = sum out-degrees over N_out(s), S_b = sum
+//            in-degrees over N_in(t); scan the smaller side; split the scan
+//            into work items of `chunk` CSR entries                  (k_plan, k_near)
+//   join     one persistent 1024-thread CTA per SM pops items from an atomic
+//            queue; the far frontier sits in a shared-memory bitmap (with a
+//            popcount rank, so the join needs no hash probe), the near rows are
+//            streamed warp-cooperatively, every hit is scored in fp32 and every
+//            path whose fp32 score can still reach the top K (within the proven
+//            fp32 error bound of the running K-th score) is kept in a
+//            shared-memory buffer; radix select + compaction bound the buffer,
+//            and the CTA's K-th score is published with atomicMax      (k_middle)
+//   merge    per query: exact K-th fp32 score over the kept candidates, the
+//            band within twice the error bound, fp64 rescoring in the
+//            canonical order, bitonic sort by the total order          (k_merge1, k_rescore, k_merge2)
+//   exact    queries whose band is too dense for the fp32 screen (ties) are
+//            recomputed with fp64 keys throughout                      (k_exact)
+//
+// Every kernel reads sizes and pointers from a device-resident PlanDev, so the
+// whole sequence is captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "mhr_internal.cuh"
+#include "mhr_query.cuh"
+#include "mhr_util.cuh"
+
+namespace mhr {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ int64_t upper_bound_i64(const int64_t* __restrict__ a, int64_t n, int64_t x) {
+    // first index i in [0, n) with a[i] > x (n if none)
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+__device__ __forceinline__ unsigned lanemask_le() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
+
+// thr - 2E rounded toward -inf, as float (conservative keep threshold)
+__device__ __forceinline__ float keep_threshold(uint32_t key, double two_err) {
+    if (key == 0u) return neg_inf();
+    return __double2float_rd(__dsub_rd(static_cast<double>(key2f(key)), two_err));
+}
+
+// path order: 1 if a ranks strictly before b
+__device__ __forceinline__ bool ranks_before(const mhr_path& a, const mhr_path& b) {
+    if (a.score != b.score) return a.score > b.score;
+    if (a.u != b.u) return a.u < b.u;
+    if (a.r1 != b.r1) return a.r1 < b.r1;
+    if (a.v != b.v) return a.v < b.v;
+    if (a.r2 != b.r2) return a.r2 < b.r2;
+    return a.r3 < b.r3;
+}
+
+__device__ __forceinline__ mhr_path worst_path() {
+    mhr_path p;
+    p.score = __longlong_as_double(0xfff0000000000000ll);  // -inf
+    p.u = p.v = 0xffffffffu;
+    p.r1 = p.r2 = p.r3 = p.pad = 0xffff;
+    return p;
+}
+
+// in-place bitonic sort of m (power of two) paths, best first; all threads call
+__device__ void block_sort_paths(mhr_path* a, int m) {
+    for (int k = 2; k <= m; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < (m >> 1); t += blockDim.x) {
+                int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+                bool asc = (i & k) == 0;
+                mhr_path x = a[i], y = a[i + j];
+                bool swap = asc ? ranks_before(y, x) : ranks_before(x, y);
+                if (swap) {
+                    a[i] = y;
+                    a[i + j] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// K-th largest order key among n keys (1 <= K <= n) by 4-pass radix select.
+// key_at(i) gives key i; all threads call; hist has 256 slots.
+template <typename KeyAt>
+__device__ uint32_t block_select_kth(KeyAt key_at, int64_t n, int K, uint32_t* hist, uint32_t* bcast) {
+    uint32_t prefix = 0, mask = 0;
+    uint32_t remaining = static_cast<uint32_t>(K);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            uint32_t k = key_at(i);
+            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (wid == 0) {
+            // lane l owns bins 255-8l .. 248-8l (descending)
+            uint32_t c = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) c += hist[255 - 8 * lane - j];
+            uint32_t cum = warp_incl_scan(c);
+            unsigned b = __ballot_sync(FULL, cum >= remaining);
+            int L = __ffs(b) - 1;
+            if (lane == L) {
+                uint32_t before = cum - c;
+                for (int j = 0; j < 8; ++j) {
+                    uint32_t bin = 255 - 8 * lane - j;
+                    uint32_t h = hist[bin];
+                    if (before + h >= remaining) {
+                        bcast[0] = prefix | (bin << shift);
+                        bcast[1] = remaining - before;
+                        break;
+                    }
+                    before += h;
+                }
+            }
+        }
+        __syncthreads();
+        prefix = bcast[0];
+        remaining = bcast[1];
+        mask |= 255u << shift;
+        __syncthreads();
+    }
+    return prefix;
+}
+
+// ===========================================================================
+// frontier expansion
+// ===========================================================================
+__global__ void k_init(const PlanDev* __restrict__ P, DevGraph g) {
+    const int nq = P->nq;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int q = tid; q < nq; q += gridDim.x * blockDim.x) {
+        const uint32_t s = P->S[q], t = P->T[q];
+        P->status[q] = (s < g.n && t < g.n && s != t) ? 0 : 1;
+        P->thr_g[q] = 0u;
+        P->dense[q] = 0;
+        P->pool_cnt[q] = 0;
+        P->band_cnt[q] = 0;
+        P->n_out[q] = 0;
+    }
+    if (tid < kCntCount) P->counters[tid] = 0ull;
+}
+
+// one warp per slot: fp32 weight, exclusion, run-head flag
+__global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, DevGraph g) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const int64_t X = P->X, totA = P->totA;
+    const int nq = P->nq;
+    for (int64_t x = warp; x < X; x += nwarps) {
+        const bool sideA = x < totA;
+        const int64_t lx = sideA ? x : x - totA;
+        const int64_t* offs = sideA ? P->a_off : P->c_off;
+        const int q = static_cast<int>(upper_bound_i64(offs, nq + 1, lx) - 1);
+        const int64_t k = lx - offs[q];
+        const uint32_t s = P->S[q], t = P->T[q];
+        uint32_t vtx, r, prev = 0xffffffffu;
+        uint32_t sdeg;
+        if (sideA) {
+            const int64_t p = g.off[s] + k;
+            vtx = g.col[p];
+            r = g.rel[p];
+            if (k > 0) prev = g.col[p - 1];
+            sdeg = static_cast<uint32_t>(g.off[vtx + 1] - g.off[vtx]);
+        } else {
+            const int64_t p = g.roff[t] + k;
+            vtx = g.rcol[p];
+            r = g.rrel[p];
+            if (k > 0) prev = g.rcol[p - 1];
+            sdeg = static_cast<uint32_t>(g.roff[vtx + 1] - g.roff[vtx]);
+        }
+        const bool excl = (vtx == s) || (vtx == t);
+        const float w = sideA ? edge_w32_group(g, s, r, vtx, lane, 32) : edge_w32_group(g, vtx, r, t, lane, 32);
+        // A vertex with no scan edges can neither be scanned nor be hit, so it
+        // never lies on a path: it is dropped from the distinct list.
+        const bool head = !excl && sdeg > 0 && (k == 0 || prev != vtx);
+        if (lane == 0) {
+            P->w32[x] = excl ? neg_inf() : w;
+            P->flag[x] = head ? 1u : 0u;
+            P->degv[x] = 0u;
+        }
+    }
+}
+
+// one thread per run head: the distinct frontier entry
+__global__ void k_lists(const PlanDev* __restrict__ P, DevGraph g) {
+    const int64_t X = P->X, totA = P->totA;
+    const int nq = P->nq;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < X; x += stride) {
+        if (!P->flag[x]) continue;
+        const bool sideA = x < totA;
+        const int64_t lx = sideA ? x : x - totA;
+        const int64_t* offs = sideA ? P->a_off : P->c_off;
+        const int q = static_cast<int>(upper_bound_i64(offs, nq + 1, lx) - 1);
+        const int64_t k = lx - offs[q];
+        const int64_t rlen = offs[q + 1] - offs[q];
+        const int64_t base = sideA ? offs[q] : totA + offs[q];
+        const int64_t j = P->scan1[x] - P->scan1[base];
+        const uint32_t s = P->S[q], t = P->T[q];
+        const uint32_t* cc = sideA ? g.col + g.off[s] : g.rcol + g.roff[t];
+        const uint32_t vtx = cc[k];
+        float mw = P->w32[x];
+        int64_t len = 1;
+        while (k + len < rlen && cc[k + len] == vtx) {
+            mw = fmaxf(mw, P->w32[x + len]);
+            ++len;
+        }
+        ListEnt e;
+        e.vertex = vtx;
+        e.run_start = static_cast<uint32_t>(k);
+        e.run_len = static_cast<uint32_t>(len);
+        e.maxw = mw;
+        if (sideA) {
+            e.deg = static_cast<uint32_t>(g.off[vtx + 1] - g.off[vtx]);
+            e.rowstart = static_cast<uint32_t>(g.off[vtx]);
+        } else {
+            e.deg = static_cast<uint32_t>(g.roff[vtx + 1] - g.roff[vtx]);
+            e.rowstart = static_cast<uint32_t>(g.roff[vtx]);
+        }
+        P->list[base + j] = e;
+        P->degv[base + j] = e.deg;
+    }
+}
+
+// single block: direction choice and the work-item queue layout
+__global__ void __launch_bounds__(1024) k_plan(const PlanDev* __restrict__ P) {
+    __shared__ int64_t sm[33];
+    const int nq = P->nq;
+    const int64_t totA = P->totA;
+    const int64_t chunk = P->chunk;
+    int64_t carry = 0;
+    for (int base = 0; base < nq; base += blockDim.x) {
+        const int q = base + threadIdx.x;
+        int64_t items = 0;
+        if (q < nq) {
+            const int64_t a0 = P->a_off[q], a1 = P->a_off[q + 1];
+            const int64_t c0 = totA + P->c_off[q], c1 = totA + P->c_off[q + 1];
+            const int64_t du = P->scan1[a1] - P->scan1[a0];
+            const int64_t dv = P->scan1[c1] - P->scan1[c0];
+            const int64_t sf = P->scan2[a1] - P->scan2[a0];
+            const int64_t sb = P->scan2[c1] - P->scan2[c0];
+            const bool fwd = sf <= sb;
+            const int64_t near_cnt = fwd ? du : dv, far_cnt = fwd ? dv : du;
+            const int64_t s_near = (P->status[q] == 0 && far_cnt > 0) ? (fwd ? sf : sb) : 0;
+            P->dir[q] = fwd ? 1 : 0;
+            P->near_cnt[q] = static_cast<int32_t>(near_cnt);
+            P->far_cnt[q] = static_cast<int32_t>(far_cnt);
+            P->s_near[q] = s_near;
+            items = (s_near + chunk - 1) / chunk;
+        }
+        int64_t tot;
+        const int64_t ex = block_excl_scan(items, sm, &tot);
+        if (q < nq) P->item_off[q] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) P->item_off[nq] = carry;
+}
+
+// near-side entries: (prefix of scan degree, row start)
+__global__ void k_near(const PlanDev* __restrict__ P) {
+    const int64_t X = P->X, totA = P->totA;
+    const int nq = P->nq;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < X; x += stride) {
+        const bool sideA = x < totA;
+        const int64_t lx = sideA ? x : x - totA;
+        const int64_t* offs = sideA ? P->a_off : P->c_off;
+        const int q = static_cast<int>(upper_bound_i64(offs, nq + 1, lx) - 1);
+        if ((P->dir[q] == 1) != sideA) continue;
+        const int64_t base = sideA ? offs[q] : totA + offs[q];
+        if (x - base >= P->near_cnt[q]) continue;
+        P->nearP[x] = make_uint2(static_cast<uint32_t>(P->scan2[x] - P->scan2[base]), P->list[x].rowstart);
+    }
+}
+
+// ===========================================================================
+// the middle join (persistent)
+// ===========================================================================
+struct MidSmem {
+    uint32_t bm[kMaxBmWords];
+    uint32_t rank[kMaxRank + 8];
+    Cand cand[kCandCap];
+    uint32_t gmap[kMaxChunk / 32 + 32];
+    uint32_t hist[256];
+    uint32_t bc[4];
+    int64_t red[33];
+    uint32_t redu[33];
+    // per-query state
+    int q, dir, near_cnt, far_cnt, local_dense, skip;
+    uint32_t s, t;
+    int64_t near_base, far_base, a_base, c_base, s_near;
+    // per-item state
+    int64_t item;
+    uint32_t e0, e1, k0, k1;
+    int cand_cnt, hit_cnt;
+    int round_cnt;  // cand_cnt snapshot taken before the barrier that opens a round
+    int pool_off;
+    uint32_t lt_key;
+    float thr_keep;
+};
+
+// block-wide in-place compaction of the candidate buffer to s32 >= thr
+__device__ void compact_cands(MidSmem& sm, float thr) {
+    const int n = sm.cand_cnt;
+    int w = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        Cand c;
+        bool keep = false;
+        if (i < n) {
+            c = sm.cand[i];
+            keep = c.s32 >= thr;
+        }
+        int tot;
+        const int pos = block_excl_scan(keep ? 1 : 0, reinterpret_cast<int*>(sm.redu), &tot);
+        if (keep) sm.cand[w + pos] = c;
+        w += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sm.cand_cnt = w;
+    __syncthreads();
+}
+
+// raise the local threshold from the buffer and the global one, then compact
+__device__ void flush_cands(MidSmem& sm, const PlanDev* __restrict__ P, int K, double two_err) {
+    const int n = sm.cand_cnt;
+    if (n >= K) {
+        const uint32_t key = block_select_kth([&](int64_t i) { return f2key(sm.cand[i].s32); }, n, K,
+                                              sm.hist, sm.bc);
+        if (threadIdx.x == 0) {
+            if (key > sm.lt_key) sm.lt_key = key;
+            atomicMax(&P->thr_g[sm.q], key);
+        }
+    }
+    if (threadIdx.x == 0) {
+        const uint32_t gk = atomicOr(&P->thr_g[sm.q], 0u);
+        if (gk > sm.lt_key) sm.lt_key = gk;
+        sm.thr_keep = keep_threshold(sm.lt_key, two_err);
+    }
+    __syncthreads();
+    compact_cands(sm, sm.thr_keep);
+    if (threadIdx.x == 0) {
+        if (sm.cand_cnt > kDenseLimit && !sm.local_dense) {
+            sm.local_dense = 1;
+            atomicExch(&P->dense[sm.q], 1);
+        }
+        sm.round_cnt = sm.cand_cnt;
+    }
+    __syncthreads();
+}
+
+// final flush of the current query into its candidate pool
+__device__ void finish_query(MidSmem& sm, const PlanDev* __restrict__ P, int K, double two_err,
+                             unsigned long long* cand_counter) {
+    if (!sm.local_dense) flush_cands(sm, P, K, two_err);
+    if (threadIdx.x == 0) {
+        sm.pool_off = -1;
+        if (!sm.local_dense && sm.cand_cnt > 0) {
+            const int n = sm.cand_cnt;
+            const int off = atomicAdd(&P->pool_cnt[sm.q], n);
+            if (off + n > P->pq) atomicExch(&P->dense[sm.q], 1);
+            else sm.pool_off = off;
+            *cand_counter += static_cast<unsigned long long>(n);
+        }
+    }
+    __syncthreads();
+    if (sm.pool_off >= 0) {
+        Cand* dst = P->pool + static_cast<int64_t>(sm.q) * P->pq + sm.pool_off;
+        for (int i = threadIdx.x; i < sm.cand_cnt; i += blockDim.x) dst[i] = sm.cand[i];
+    }
+    __syncthreads();
+}
+
+__device__ void setup_query(MidSmem& sm, const PlanDev* __restrict__ P, int q) {
+    if (threadIdx.x == 0) {
+        sm.q = q;
+        sm.s = P->S[q];
+        sm.t = P->T[q];
+        sm.dir = P->dir[q];
+        sm.near_cnt = P->near_cnt[q];
+        sm.far_cnt = P->far_cnt[q];
+        sm.s_near = P->s_near[q];
+        sm.a_base = P->a_off[q];
+        sm.c_base = P->totA + P->c_off[q];
+        sm.near_base = sm.dir ? sm.a_base : sm.c_base;
+        sm.far_base = sm.dir ? sm.c_base : sm.a_base;
+        sm.cand_cnt = 0;
+        sm.lt_key = 0u;
+        sm.thr_keep = neg_inf();
+        sm.local_dense = 0;
+    }
+    const int nbw = P->nbw;
+    for (int i = threadIdx.x; i < nbw; i += blockDim.x) sm.bm[i] = 0u;
+    __syncthreads();
+    const int sigma = P->sigma;
+    const ListEnt* far = P->list + sm.far_base;
+    for (int k = threadIdx.x; k < sm.far_cnt; k += blockDim.x) {
+        const uint32_t bv = far[k].vertex >> sigma;
+        atomicOr(&sm.bm[bv >> 5], 1u << (bv & 31u));
+    }
+    __syncthreads();
+    if (sigma == 0) {
+        // rank[b] = set bits in words [0, 8b)
+        const int nblk = (nbw + kRankWords - 1) / kRankWords;
+        const int per = (nblk + blockDim.x - 1) / blockDim.x;  // <= 4
+        int mine[4] = {0, 0, 0, 0};
+        int sum = 0;
+        for (int j = 0; j < per; ++j) {
+            const int b = threadIdx.x * per + j;
+            int c = 0;
+            if (b < nblk)
+                for (int w = b * kRankWords; w < min(nbw, (b + 1) * kRankWords); ++w) c += __popc(sm.bm[w]);
+            mine[j] = c;
+            sum += c;
+        }
+        int tot;
+        int ex = block_excl_scan(sum, reinterpret_cast<int*>(sm.redu), &tot);
+        for (int j = 0; j < per; ++j) {
+            const int b = threadIdx.x * per + j;
+            if (b < nblk) sm.rank[b] = static_cast<uint32_t>(ex);
+            ex += mine[j];
+        }
+    }
+    __syncthreads();
+}
+
+template <int UNROLL>
+__global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __restrict__ P, DevGraph g) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MidSmem& sm = *reinterpret_cast<MidSmem*>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int K = P->K;
+    const int nq = P->nq;
+    const int sigma = P->sigma;
+    const double two_err = 2.0 * P->err_path;
+    const int64_t total_items = P->item_off[nq];
+    Hit* hits = P->hits + static_cast<int64_t>(blockIdx.x) * kMaxChunk;
+    unsigned long long n_scanned = 0, n_hits = 0, n_cands = 0;
+    int cur_q = -1;
+    if (threadIdx.x == 0) sm.q = -1;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int64_t it = static_cast<int64_t>(atomicAdd(&P->counters[kCntItem], 1ull));
+            sm.item = it;
+            if (it < total_items) {
+                const int q = static_cast<int>(upper_bound_i64(P->item_off, nq + 1, it) - 1);
+                sm.skip = q;  // temporarily: the item's query
+            }
+        }
+        __syncthreads();
+        const int64_t item = sm.item;
+        if (item >= total_items) break;
+        const int q = sm.skip;
+        __syncthreads();
+        if (q != cur_q) {
+            if (cur_q >= 0) finish_query(sm, P, K, two_err, &n_cands);
+            setup_query(sm, P, q);
+            cur_q = q;
+        }
+        if (threadIdx.x == 0) {
+            sm.skip = sm.local_dense || atomicOr(&P->dense[q], 0) != 0;
+            const int64_t e0 = (item - P->item_off[q]) * P->chunk;
+            const int64_t e1 = min(e0 + static_cast<int64_t>(P->chunk), sm.s_near);
+            sm.e0 = static_cast<uint32_t>(e0);
+            sm.e1 = static_cast<uint32_t>(e1);
+            sm.hit_cnt = 0;
+        } else if (threadIdx.x == 32 || threadIdx.x == 64) {
+            // largest near index whose prefix is <= e (e = e0 or e1 - 1)
+            const int64_t e0 = (item - P->item_off[q]) * P->chunk;
+            const int64_t e1 = min(e0 + static_cast<int64_t>(P->chunk), P->s_near[q]);
+            const int64_t e = threadIdx.x == 32 ? e0 : e1 - 1;
+            const int64_t nb = P->dir[q] ? P->a_off[q] : P->totA + P->c_off[q];
+            int lo = 0, hi = P->near_cnt[q];
+            while (lo + 1 < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (static_cast<int64_t>(P->nearP[nb + mid].x) <= e) lo = mid;
+                else hi = mid;
+            }
+            if (threadIdx.x == 32) sm.k0 = lo;
+            else sm.k1 = lo;
+        }
+        __syncthreads();
+        if (sm.skip) continue;
+
+        const uint32_t e0 = sm.e0, e1 = sm.e1;
+        const int ngroups = static_cast<int>((e1 - e0 + 31) / 32);
+        const int near_cnt = sm.near_cnt;
+        const uint2* nearP = P->nearP + sm.near_base;
+        const uint32_t s_near32 = static_cast<uint32_t>(sm.s_near);
+        // --- group -> owning near entry (+1), by marking group starts then a prefix max
+        for (int i = threadIdx.x; i < ngroups; i += blockDim.x) sm.gmap[i] = 0u;
+        __syncthreads();
+        for (uint32_t k = sm.k0 + threadIdx.x; k <= sm.k1; k += blockDim.x) {
+            const uint32_t pk = nearP[k].x;
+            const uint32_t pk1 = (k + 1 < static_cast<uint32_t>(near_cnt)) ? nearP[k + 1].x : s_near32;
+            const uint32_t lo = max(pk, e0), hi = min(pk1, e1);
+            const uint32_t gf = (lo - e0 + 31) / 32;
+            if (e0 + 32 * gf < hi) sm.gmap[gf] = k + 1;
+        }
+        __syncthreads();
+        {
+            // inclusive prefix max over <= 512 entries (one per thread)
+            uint32_t v = threadIdx.x < ngroups ? sm.gmap[threadIdx.x] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(FULL, v, o);
+                if (lane >= o) v = max(v, y);
+            }
+            if (lane == 31) sm.redu[warp] = v;
+            __syncthreads();
+            if (warp == 0) {
+                uint32_t w = sm.redu[lane];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(FULL, w, o);
+                    if (lane >= o) w = max(w, y);
+                }
+                sm.redu[lane] = w;
+            }
+            __syncthreads();
+            if (warp > 0) v = max(v, sm.redu[warp - 1]);
+            if (threadIdx.x < ngroups) sm.gmap[threadIdx.x] = v;
+        }
+        __syncthreads();
+
+        // --- scan: stream near rows, probe the far bitmap, stage hits
+        const uint32_t* colsrc = sm.dir ? g.col : g.rcol;
+        const ListEnt* far = P->list + sm.far_base;
+        const int far_cnt = sm.far_cnt;
+        for (int gb = warp * UNROLL; gb < ngroups; gb += kMidWarps * UNROLL) {
+            uint2 ne[UNROLL];
+            uint32_t kk[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const int gidx = gb + u;
+                ne[u] = make_uint2(s_near32, 0u);
+                kk[u] = 0;
+                if (gidx < ngroups) {
+                    kk[u] = sm.gmap[gidx] - 1u;
+                    const uint32_t idx = kk[u] + lane;
+                    if (idx < static_cast<uint32_t>(near_cnt)) ne[u] = nearP[idx];
+                }
+            }
+            uint32_t xv[UNROLL], epos[UNROLL], nk[UNROLL];
+            bool valid[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const int gidx = gb + u;
+                valid[u] = false;
+                xv[u] = 0;
+                epos[u] = 0;
+                nk[u] = 0;
+                if (gidx < ngroups) {
+                    const uint32_t gs = e0 + 32u * gidx;
+                    const uint32_t e = gs + lane;
+                    const uint32_t pos = ne[u].x - gs;
+                    const uint32_t bit = (lane >= 1 && pos >= 1 && pos <= 31) ? (1u << pos) : 0u;
+                    const uint32_t mask = __reduce_or_sync(FULL, bit);
+                    const int c = __popc(mask & lanemask_le());
+                    const uint32_t pm = __shfl_sync(FULL, ne[u].x, c);
+                    const uint32_t rs = __shfl_sync(FULL, ne[u].y, c);
+                    valid[u] = e < e1;
+                    epos[u] = rs + (e - pm);
+                    nk[u] = kk[u] + c;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u)
+                if (valid[u]) xv[u] = __ldg(colsrc + epos[u]);
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const int gidx = gb + u;
+                if (gidx >= ngroups) break;
+                bool hit = false;
+                uint32_t fk = 0;
+                if (valid[u]) {
+                    const uint32_t x = xv[u];
+                    const uint32_t bv = x >> sigma;
+                    const uint32_t word = sm.bm[bv >> 5];
+                    if ((word >> (bv & 31u)) & 1u) {
+                        if (sigma == 0) {
+                            const uint32_t wi = x >> 5;
+                            uint32_t r = sm.rank[x >> 8];
+                            for (uint32_t w = (x >> 8) << 3; w < wi; ++w) r += __popc(sm.bm[w]);
+                            fk = r + __popc(word & ((1u << (x & 31u)) - 1u));
+                            hit = true;
+                        } else {
+                            int lo = 0, hi = far_cnt;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (far[mid].vertex < x) lo = mid + 1;
+                                else hi = mid;
+                            }
+                            if (lo < far_cnt && far[lo].vertex == x) {
+                                fk = static_cast<uint32_t>(lo);
+                                hit = true;
+                            }
+                        }
+                    }
+                }
+                const unsigned b = __ballot_sync(FULL, hit);
+                if (b) {
+                    int base = 0;
+                    const int leader = __ffs(b) - 1;
+                    if (lane == leader) base = atomicAdd(&sm.hit_cnt, __popc(b));
+                    base = __shfl_sync(FULL, base, leader);
+                    if (hit) {
+                        Hit h;
+                        h.near_k = nk[u];
+                        h.far_k = fk;
+                        h.epos = epos[u];
+                        hits[base + __popc(b & lanemask_lt())] = h;
+                    }
+                }
+            }
+        }
+        if (threadIdx.x == 0) sm.round_cnt = sm.cand_cnt;
+        __syncthreads();
+        const int nh = sm.hit_cnt;
+        if (threadIdx.x == 0) {
+            n_scanned += e1 - e0;
+            n_hits += static_cast<unsigned long long>(nh);
+        }
+
+        // --- score hits; keep paths that can still reach the top K
+        const uint16_t* relsrc = sm.dir ? g.rel : g.rrel;
+        const ListEnt* nearL = P->list + sm.near_base;
+        const float* w1s = P->w32 + sm.a_base;
+        const float* w3s = P->w32 + sm.c_base;
+        int h = warp;
+        uint32_t slice = 0;
+        bool have_w2 = false;
+        float w2 = 0.f;
+        for (;;) {
+            const int budget = (kCandCap - sm.round_cnt) / kMidWarps;
+            int used = 0;
+            bool done = true;
+            if (!sm.local_dense) {
+                const float thr = sm.thr_keep;
+                while (h < nh) {
+                    const Hit ht = hits[h];
+                    const ListEnt ne = nearL[ht.near_k];
+                    const ListEnt fe = far[ht.far_k];
+                    const ListEnt& ea = sm.dir ? ne : fe;  // hop-1 side (u)
+                    const ListEnt& ec = sm.dir ? fe : ne;  // hop-3 side (v)
+                    if (!have_w2) {
+                        const uint32_t r2 = relsrc[ht.epos];
+                        w2 = edge_w32_group(g, ea.vertex, r2, ec.vertex, lane, 32);
+                        have_w2 = true;
+                        slice = 0;
+                        const float smax = __fadd_rn(__fadd_rn(ea.maxw, w2), ec.maxw);
+                        if (smax < thr) {
+                            h += kMidWarps;
+                            have_w2 = false;
+                            continue;
+                        }
+                    }
+                    const uint32_t na = ea.run_len, nc = ec.run_len;
+                    const uint32_t total = na * nc;
+                    bool stop = false;
+                    while (slice < total) {
+                        const uint32_t c = slice + lane;
+                        bool keep = false;
+                        Cand cd;
+                        if (c < total) {
+                            const uint32_t i = c / nc, j = c - i * nc;
+                            const float w1 = w1s[ea.run_start + i];
+                            const float w3 = w3s[ec.run_start + j];
+                            const float s32 = __fadd_rn(__fadd_rn(w1, w2), w3);
+                            keep = s32 >= thr;
+                            cd.s32 = s32;
+                            cd.a_idx = ea.run_start + i;
+                            cd.c_idx = ec.run_start + j;
+                            cd.r2 = relsrc[ht.epos];
+                            cd.pad = 0;
+                        }
+                        const unsigned b = __ballot_sync(FULL, keep);
+                        const int nk2 = __popc(b);
+                        if (used + nk2 > budget) {
+                            stop = true;
+                            break;
+                        }
+                        if (nk2) {
+                            int base = 0;
+                            const int leader = __ffs(b) - 1;
+                            if (lane == leader) base = atomicAdd(&sm.cand_cnt, nk2);
+                            base = __shfl_sync(FULL, base, leader);
+                            if (keep) sm.cand[base + __popc(b & lanemask_lt())] = cd;
+                        }
+                        used += nk2;
+                        slice += 32;
+                    }
+                    if (stop) {
+                        done = false;
+                        break;
+                    }
+                    h += kMidWarps;
+                    have_w2 = false;
+                }
+            }
+            if (!__syncthreads_or(done ? 0 : 1)) break;
+            flush_cands(sm, P, K, two_err);
+        }
+        __syncthreads();
+    }
+    if (cur_q >= 0) finish_query(sm, P, K, two_err, &n_cands);
+    if (threadIdx.x == 0) {
+        atomicAdd(&P->counters[kCntScanned], n_scanned);
+        atomicAdd(&P->counters[kCntHits], n_hits);
+        atomicAdd(&P->counters[kCntCands], n_cands);
+    }
+}
+
+// ===========================================================================
+// merge: exact K-th fp32 score, band, fp64 rescoring, final order
+// ===========================================================================
+__global__ void __launch_bounds__(1024) k_merge1(const PlanDev* __restrict__ P) {
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t bc[4];
+    __shared__ int red[33];
+    __shared__ float s_thr;
+    const int K = P->K;
+    const double two_err = 2.0 * P->err_path;
+    for (int q = blockIdx.x; q < P->nq; q += gridDim.x) {
+        if (P->status[q] != 0 || P->dense[q] != 0) continue;
+        const int pc = P->pool_cnt[q];
+        if (pc > P->pq) continue;
+        const Cand* pool = P->pool + static_cast<int64_t>(q) * P->pq;
+        if (threadIdx.x == 0) s_thr = neg_inf();
+        __syncthreads();
+        if (pc >= K) {
+            const uint32_t key = block_select_kth([&](int64_t i) { return f2key(pool[i].s32); }, pc, K, hist, bc);
+            if (threadIdx.x == 0) s_thr = keep_threshold(key, two_err);
+        }
+        __syncthreads();
+        const float thr = s_thr;
+        Cand* band = P->band_cand + static_cast<int64_t>(q) * P->band_cap;
+        int w = 0;
+        for (int base = 0; base < pc; base += blockDim.x) {
+            const int i = base + threadIdx.x;
+            bool keep = false;
+            Cand c;
+            if (i < pc) {
+                c = pool[i];
+                keep = c.s32 >= thr;
+            }
+            int tot;
+            const int pos = block_excl_scan(keep ? 1 : 0, red, &tot);
+            if (keep && w + pos < P->band_cap) band[w + pos] = c;
+            w += tot;
+        }
+        if (threadIdx.x == 0) {
+            if (w > P->band_cap) {
+                atomicExch(&P->dense[q], 1);
+                P->band_cnt[q] = 0;
+            } else {
+                P->band_cnt[q] = w;
+                atomicAdd(&P->counters[kCntRescored], static_cast<unsigned long long>(w));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_rescore(const PlanDev* __restrict__ P, DevGraph g) {
+    const int64_t total = static_cast<int64_t>(P->nq) * P->band_cap;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total; x += stride) {
+        const int q = static_cast<int>(x / P->band_cap);
+        const int i = static_cast<int>(x - static_cast<int64_t>(q) * P->band_cap);
+        if (i >= P->band_cnt[q] || P->dense[q]) continue;
+        const Cand c = P->band_cand[x];
+        const uint32_t s = P->S[q], t = P->T[q];
+        const int64_t p1 = g.off[s] + c.a_idx;
+        const int64_t p3 = g.roff[t] + c.c_idx;
+        mhr_path p;
+        p.u = g.col[p1];
+        p.r1 = g.rel[p1];
+        p.v = g.rcol[p3];
+        p.r3 = g.rrel[p3];
+        p.r2 = c.r2;
+        p.pad = 0;
+        const double w1 = edge_w64(g, s, p.r1, p.u);
+        const double w2 = edge_w64(g, p.u, p.r2, p.v);
+        const double w3 = edge_w64(g, p.v, p.r3, t);
+        p.score = __dadd_rn(__dadd_rn(w1, w2), w3);
+        P->band_path[x] = p;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_merge2(const PlanDev* __restrict__ P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    mhr_path* buf = reinterpret_cast<mhr_path*>(smem_raw);
+    const int K = P->K;
+    for (int q = blockIdx.x; q < P->nq; q += gridDim.x) {
+        if (P->status[q] != 0) {
+            if (threadIdx.x == 0) P->n_out[q] = -1;
+            continue;
+        }
+        if (P->dense[q]) continue;
+        const int nb = P->band_cnt[q];
+        int m = 2;
+        while (m < nb) m <<= 1;
+        const mhr_path* src = P->band_path + static_cast<int64_t>(q) * P->band_cap;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) buf[i] = i < nb ? src[i] : worst_path();
+        __syncthreads();
+        block_sort_paths(buf, m);
+        const int nout = min(nb, K);
+        mhr_path* dst = P->out + static_cast<int64_t>(q) * K;
+        for (int i = threadIdx.x; i < nout; i += blockDim.x) dst[i] = buf[i];
+        if (threadIdx.x == 0) P->n_out[q] = nout;
+        __syncthreads();
+    }
+}
+
+// ===========================================================================
+// exact path for tie-heavy queries: fp64 keys for every candidate that the
+// fp32 screen cannot separate from the running K-th score
+// ===========================================================================
+constexpr int kExactBuf = 4096;
+constexpr int kExactTile = 1024;
+
+struct ExactSmem {
+    mhr_path buf[kExactBuf];  // [0, K) top K, [K, ...) staging
+    uint32_t hnk[kExactTile], hfk[kExactTile], hep[kExactTile];
+    float hw2[kExactTile];
+    int64_t hcomb[kExactTile + 1];
+    int64_t red[33];
+    int nt, ns, hit_cnt;
+    double thr64;
+};
+
+__device__ void exact_flush(ExactSmem& sm, int K) {
+    __syncthreads();
+    const int nt = sm.nt, ns = sm.ns;
+    for (int i = threadIdx.x; i < kExactBuf; i += blockDim.x) {
+        const bool live = (i < nt) || (i >= K && i < K + ns);
+        if (!live) sm.buf[i] = worst_path();
+    }
+    __syncthreads();
+    block_sort_paths(sm.buf, kExactBuf);
+    if (threadIdx.x == 0) {
+        sm.nt = min(K, nt + ns);
+        sm.ns = 0;
+        if (sm.nt == K) sm.thr64 = sm.buf[K - 1].score;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_exact(const PlanDev* __restrict__ P, DevGraph g) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ExactSmem& sm = *reinterpret_cast<ExactSmem*>(smem_raw);
+    const int K = P->K;
+    const double err = P->err_path;
+    for (int q = blockIdx.x; q < P->nq; q += gridDim.x) {
+        if (P->status[q] != 0 || !P->dense[q]) continue;
+        if (threadIdx.x == 0) {
+            sm.nt = 0;
+            sm.ns = 0;
+            sm.thr64 = __longlong_as_double(0xfff0000000000000ll);
+            atomicAdd(&P->counters[kCntDense], 1ull);
+        }
+        __syncthreads();
+        const uint32_t s = P->S[q], t = P->T[q];
+        const int dir = P->dir[q];
+        const int64_t a_base = P->a_off[q], c_base = P->totA + P->c_off[q];
+        const int64_t nb = dir ? a_base : c_base, fb = dir ? c_base : a_base;
+        const int near_cnt = P->near_cnt[q], far_cnt = P->far_cnt[q];
+        const int64_t s_near = P->s_near[q];
+        const uint2* nearP = P->nearP + nb;
+        const ListEnt* nearL = P->list + nb;
+        const ListEnt* far = P->list + fb;
+        const uint32_t* colsrc = dir ? g.col : g.rcol;
+        const uint16_t* relsrc = dir ? g.rel : g.rrel;
+        for (int64_t eb = 0; eb < s_near; eb += kExactTile) {
+            if (threadIdx.x == 0) sm.hit_cnt = 0;
+            __syncthreads();
+            const int64_t e = eb + threadIdx.x;
+            if (e < s_near) {
+                int lo = 0, hi = near_cnt;
+                while (lo + 1 < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (static_cast<int64_t>(nearP[mid].x) <= e) lo = mid;
+                    else hi = mid;
+                }
+                const uint32_t ep = nearP[lo].y + static_cast<uint32_t>(e - nearP[lo].x);
+                const uint32_t x = colsrc[ep];
+                int a = 0, b = far_cnt;
+                while (a < b) {
+                    const int mid = (a + b) >> 1;
+                    if (far[mid].vertex < x) a = mid + 1;
+                    else b = mid;
+                }
+                if (a < far_cnt && far[a].vertex == x) {
+                    const ListEnt& ne = nearL[lo];
+                    const ListEnt& fe = far[a];
+                    const ListEnt& ea = dir ? ne : fe;
+                    const ListEnt& ec = dir ? fe : ne;
+                    const int slot = atomicAdd(&sm.hit_cnt, 1);
+                    sm.hnk[slot] = lo;
+                    sm.hfk[slot] = a;
+                    sm.hep[slot] = ep;
+                    sm.hw2[slot] = edge_w32_group(g, ea.vertex, relsrc[ep], ec.vertex, 0, 1);
+                }
+            }
+            __syncthreads();
+            const int nh = sm.hit_cnt;
+            int64_t comb = 0;
+            if (threadIdx.x < nh) {
+                const ListEnt& ne = nearL[sm.hnk[threadIdx.x]];
+                const ListEnt& fe = far[sm.hfk[threadIdx.x]];
+                comb = static_cast<int64_t>(ne.run_len) * fe.run_len;
+            }
+            int64_t tot;
+            const int64_t ex = block_excl_scan(comb, sm.red, &tot);
+            if (threadIdx.x < nh) sm.hcomb[threadIdx.x] = ex;
+            if (threadIdx.x == 0) sm.hcomb[nh] = tot;
+            __syncthreads();
+            for (int64_t cb = 0; cb < tot; cb += blockDim.x) {
+                if (sm.ns + static_cast<int>(blockDim.x) > kExactBuf - K) exact_flush(sm, K);
+                const int64_t c = cb + threadIdx.x;
+                if (c < tot) {
+                    int lo = 0, hi = nh;  // largest h with hcomb[h] <= c
+                    while (lo + 1 < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sm.hcomb[mid] <= c) lo = mid;
+                        else hi = mid;
+                    }
+                    const ListEnt& ne = nearL[sm.hnk[lo]];
+                    const ListEnt& fe = far[sm.hfk[lo]];
+                    const ListEnt& ea = dir ? ne : fe;
+                    const ListEnt& ec = dir ? fe : ne;
+                    const int64_t local = c - sm.hcomb[lo];
+                    const uint32_t i = static_cast<uint32_t>(local / ec.run_len);
+                    const uint32_t j = static_cast<uint32_t>(local - static_cast<int64_t>(i) * ec.run_len);
+                    const float w1 = P->w32[a_base + ea.run_start + i];
+                    const float w3 = P->w32[c_base + ec.run_start + j];
+                    const float s32 = __fadd_rn(__fadd_rn(w1, sm.hw2[lo]), w3);
+                    const double thr = sm.thr64;
+                    if (static_cast<double>(s32) + err >= thr) {
+                        const int64_t p1 = g.off[s] + ea.run_start + i;
+                        const int64_t p3 = g.roff[t] + ec.run_start + j;
+                        mhr_path p;
+                        p.u = ea.vertex;
+                        p.v = ec.vertex;
+                        p.r1 = g.rel[p1];
+                        p.r3 = g.rrel[p3];
+                        p.r2 = relsrc[sm.hep[lo]];
+                        p.pad = 0;
+                        const double w1d = edge_w64(g, s, p.r1, p.u);
+                        const double w2d = edge_w64(g, p.u, p.r2, p.v);
+                        const double w3d = edge_w64(g, p.v, p.r3, t);
+                        p.score = __dadd_rn(__dadd_rn(w1d, w2d), w3d);
+                        if (p.score >= thr) {
+                            const int slot = atomicAdd(&sm.ns, 1);
+                            sm.buf[K + slot] = p;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            __syncthreads();
+        }
+        exact_flush(sm, K);
+        mhr_path* dst = P->out + static_cast<int64_t>(q) * K;
+        for (int i = threadIdx.x; i < sm.nt; i += blockDim.x) dst[i] = sm.buf[i];
+        if (threadIdx.x == 0) P->n_out[q] = sm.nt;
+        __syncthreads();
+    }
+}
+
+// ===========================================================================
+// host side: plans (buffers + captured graph) per (nq, K, chunk)
+// ===========================================================================
+struct Plan {
+    int nq = 0, K = 0, chunk = 0, grid = 0;
+    PlanDev h{};
+    unsigned char* dregion = nullptr;  // [PlanDev][S][T][a_off][c_off]
+    size_t region_bytes = 0;
+    unsigned char* pin = nullptr;      // pinned host mirror of dregion
+    std::vector<void*> fixed;
+    void* slot_mem = nullptr;
+    int64_t slot_cap = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t h2d_done = nullptr;
+    bool h2d_pending = false;
+    ~Plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (cap) cudaStreamDestroy(cap);
+        if (h2d_done) cudaEventDestroy(h2d_done);
+        for (void* p : fixed) cudaFree(p);
+        if (slot_mem) cudaFree(slot_mem);
+        if (dregion) cudaFree(dregion);
+        if (pin) cudaFreeHost(pin);
+    }
+};
+
+struct PlanCache {
+    std::map<std::tuple<int, int, int>, Plan*> plans;
+    ~PlanCache() {
+        for (auto& kv : plans) delete kv.second;
+    }
+};
+
+void destroy_plans(mhr_graph* g) {
+    delete g->plans;
+    g->plans = nullptr;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct RegionLayout {
+    size_t off_S, off_T, off_a, off_c, total;
+};
+
+static RegionLayout region_layout(int nq) {
+    RegionLayout L;
+    size_t o = align_up(sizeof(PlanDev), 256);
+    L.off_S = o;
+    o = align_up(o + sizeof(uint32_t) * nq, 256);
+    L.off_T = o;
+    o = align_up(o + sizeof(uint32_t) * nq, 256);
+    L.off_a = o;
+    o = align_up(o + sizeof(int64_t) * (nq + 1), 256);
+    L.off_c = o;
+    o = align_up(o + sizeof(int64_t) * (nq + 1), 256);
+    L.total = o;
+    return L;
+}
+
+template <typename T>
+static mhr_status plan_alloc(Plan* p, T** out, size_t count) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, std::max<size_t>(count * sizeof(T), 16));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (query plan)");
+    p->fixed.push_back(ptr);
+    *out = static_cast<T*>(ptr);
+    return MHR_OK;
+}
+
+static size_t mid_smem_bytes() { return sizeof(MidSmem); }
+static size_t exact_smem_bytes() { return sizeof(ExactSmem); }
+static size_t merge2_smem_bytes(int band_cap) {
+    int m = 2;
+    while (m < band_cap) m <<= 1;
+    return sizeof(mhr_path) * m;
+}
+
+static mhr_status ensure_slots(Plan* p, int64_t X) {
+    if (X <= p->slot_cap && p->slot_mem) return MHR_OK;
+    int64_t cap = std::max<int64_t>(X, std::max<int64_t>(p->slot_cap * 2, 1 << 16));
+    // per slot: w32 4, flag 4, degv 4, scan1 8, scan2 8, list 24, nearP 8
+    const size_t a8 = 256;
+    size_t o = 0;
+    const size_t o_w32 = o; o = align_up(o + 4 * cap, a8);
+    const size_t o_flag = o; o = align_up(o + 4 * cap, a8);
+    const size_t o_degv = o; o = align_up(o + 4 * cap, a8);
+    const size_t o_s1 = o; o = align_up(o + 8 * (cap + 1), a8);
+    const size_t o_s2 = o; o = align_up(o + 8 * (cap + 1), a8);
+    const size_t o_list = o; o = align_up(o + sizeof(ListEnt) * cap, a8);
+    const size_t o_near = o; o = align_up(o + sizeof(uint2) * cap, a8);
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, o);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (frontier slots)");
+    if (p->slot_mem) {
+        cudaDeviceSynchronize();
+        cudaFree(p->slot_mem);
+    }
+    p->slot_mem = mem;
+    p->slot_cap = cap;
+    unsigned char* b = static_cast<unsigned char*>(mem);
+    p->h.w32 = reinterpret_cast<float*>(b + o_w32);
+    p->h.flag = reinterpret_cast<uint32_t*>(b + o_flag);
+    p->h.degv = reinterpret_cast<uint32_t*>(b + o_degv);
+    p->h.scan1 = reinterpret_cast<int64_t*>(b + o_s1);
+    p->h.scan2 = reinterpret_cast<int64_t*>(b + o_s2);
+    p->h.list = reinterpret_cast<ListEnt*>(b + o_list);
+    p->h.nearP = reinterpret_cast<uint2*>(b + o_near);
+    // scan kernels take raw pointers, so a new buffer needs a new capture
+    if (p->exec) {
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
+    return MHR_OK;
+}
+
+static cudaError_t launch_sequence(Plan* p, const mhr_graph* G, cudaStream_t st) {
+    const PlanDev* d = reinterpret_cast<const PlanDev*>(p->dregion);
+    const int sms = std::max(1, G->num_sms);
+    const DevGraph& g = G->dg;
+    const int64_t* nX = reinterpret_cast<const int64_t*>(p->dregion + offsetof(PlanDev, X));
+    k_init<<<std::max(1, std::min(sms, (p->nq + 255) / 256)), 256, 0, st>>>(d, g);
+    k_expand<<<sms * 8, 256, 0, st>>>(d, g);
+    cudaError_t e = device_excl_scan<uint32_t>(p->h.flag, nX, p->h.partials, p->h.scan1, st);
+    if (e != cudaSuccess) return e;
+    k_lists<<<sms * 4, 256, 0, st>>>(d, g);
+    e = device_excl_scan<uint32_t>(p->h.degv, nX, p->h.partials, p->h.scan2, st);
+    if (e != cudaSuccess) return e;
+    k_plan<<<1, 1024, 0, st>>>(d);
+    k_near<<<sms * 4, 256, 0, st>>>(d);
+    k_middle<kUnroll><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
+    k_merge1<<<std::min(p->nq, sms * 2), 1024, 0, st>>>(d);
+    k_rescore<<<sms * 4, 128, 0, st>>>(d, g);
+    k_merge2<<<std::min(p->nq, sms * 2), 1024, merge2_smem_bytes(p->h.band_cap), st>>>(d);
+    k_exact<<<std::min(p->nq, sms * 2), 1024, exact_smem_bytes(), st>>>(d, g);
+    return cudaGetLastError();
+}
+
+static mhr_status capture(Plan* p, const mhr_graph* G) {
+    if (p->exec) return MHR_OK;
+    cudaGraph_t graph = nullptr;
+    MHR_CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = launch_sequence(p, G, p->cap);
+    cudaError_t e2 = cudaStreamEndCapture(p->cap, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e, "kernel launch during capture");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&p->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return MHR_OK;
+}
+
+static int choose_sigma(int64_t n) {
+    int sigma = 0;
+    while (((n - 1) >> sigma) >= static_cast<int64_t>(kMaxBmWords) * 32) ++sigma;
+    return sigma;
+}
+
+static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) {
+    Plan* p = new Plan();
+    p->nq = nq;
+    p->K = K;
+    p->chunk = chunk;
+    p->grid = std::max(1, G->num_sms);
+    PlanDev& h = p->h;
+    h.nq = nq;
+    h.K = K;
+    h.chunk = chunk;
+    h.sigma = choose_sigma(G->dg.n);
+    h.nbw = static_cast<int32_t>(((G->dg.n - 1) >> h.sigma) / 32 + 1);
+    h.pq = 8 * K + 2048;
+    h.band_cap = K + 2048;
+    h.err_path = G->err_path;
+    mhr_status rc = MHR_OK;
+    auto bail = [&](mhr_status r) {
+        delete p;
+        return r;
+    };
+    if ((rc = plan_alloc(p, &h.status, nq)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.dir, nq)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.near_cnt, nq)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.far_cnt, nq)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.s_near, nq)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.item_off, nq + 1)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.thr_g, nq)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.dense, nq)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.pool_cnt, nq)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.band_cnt, nq)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.hits, static_cast<size_t>(p->grid) * kMaxChunk)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.pool, static_cast<size_t>(nq) * h.pq)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.band_cand, static_cast<size_t>(nq) * h.band_cap)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.band_path, static_cast<size_t>(nq) * h.band_cap)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.out, static_cast<size_t>(nq) * K)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.n_out, nq)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.counters, kCntCount)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.partials, kScanGrid + 1)) != MHR_OK) return bail(rc);
+    const RegionLayout L = region_layout(nq);
+    p->region_bytes = L.total;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p->dregion), L.total);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc (plan region)"));
+    e = cudaMallocHost(reinterpret_cast<void**>(&p->pin), L.total);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocHost (plan region)"));
+    h.S = reinterpret_cast<const uint32_t*>(p->dregion + L.off_S);
+    h.T = reinterpret_cast<const uint32_t*>(p->dregion + L.off_T);
+    h.a_off = reinterpret_cast<const int64_t*>(p->dregion + L.off_a);
+    h.c_off = reinterpret_cast<const int64_t*>(p->dregion + L.off_c);
+    e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
+    e = cudaEventCreateWithFlags(&p->h2d_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+    e = cudaFuncSetAttribute(k_middle<kUnroll>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(mid_smem_bytes()));
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaFuncSetAttribute (middle join)"));
+    e = cudaFuncSetAttribute(k_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(exact_smem_bytes()));
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaFuncSetAttribute (exact)"));
+    e = cudaFuncSetAttribute(k_merge2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(merge2_smem_bytes(h.band_cap)));
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaFuncSetAttribute (merge)"));
+    *out = p;
+    return MHR_OK;
+}
+
+static mhr_status get_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) {
+    if (!G->plans) G->plans = new PlanCache();
+    auto key = std::make_tuple(nq, K, chunk);
+    auto it = G->plans->plans.find(key);
+    if (it != G->plans->plans.end()) {
+        *out = it->second;
+        return MHR_OK;
+    }
+    if (G->plans->plans.size() >= 8) {
+        cudaDeviceSynchronize();
+        delete G->plans->plans.begin()->second;
+        G->plans->plans.erase(G->plans->plans.begin());
+    }
+    Plan* p = nullptr;
+    MHR_TRY(make_plan(G, nq, K, chunk, &p));
+    G->plans->plans[key] = p;
+    *out = p;
+    return MHR_OK;
+}
+
+static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint32_t* hT, int K,
+                            const mhr_query_opts* opts, cudaStream_t st, Plan** plan_out) {
+    int chunk = (opts && opts->chunk > 0) ? opts->chunk : kDefaultChunk;
+    if (chunk > kMaxChunk || chunk < 32 || (chunk & 31))
+        return fail(MHR_EINVAL, "opts->chunk must be a multiple of 32 in [32, 16384]");
+    Plan* p = nullptr;
+    MHR_TRY(get_plan(G, nq, K, chunk, &p));
+    // sizes from the host copy of the row starts
+    const RegionLayout L = region_layout(nq);
+    if (p->h2d_pending) {
+        MHR_CUDA_TRY(cudaEventSynchronize(p->h2d_done));
+        p->h2d_pending = false;
+    }
+    uint32_t* pS = reinterpret_cast<uint32_t*>(p->pin + L.off_S);
+    uint32_t* pT = reinterpret_cast<uint32_t*>(p->pin + L.off_T);
+    int64_t* pa = reinterpret_cast<int64_t*>(p->pin + L.off_a);
+    int64_t* pc = reinterpret_cast<int64_t*>(p->pin + L.off_c);
+    const int64_t n = G->dg.n;
+    int64_t ta = 0, tc = 0;
+    for (int q = 0; q < nq; ++q) {
+        const uint32_t s = hS[q], t = hT[q];
+        pS[q] = s;
+        pT[q] = t;
+        pa[q] = ta;
+        pc[q] = tc;
+        if (s < n && t < n && s != t) {
+            ta += G->h_off[s + 1] - G->h_off[s];
+            tc += G->h_roff[t + 1] - G->h_roff[t];
+        }
+    }
+    pa[nq] = ta;
+    pc[nq] = tc;
+    MHR_TRY(ensure_slots(p, ta + tc));
+    p->h.X = ta + tc;
+    p->h.totA = ta;
+    std::memcpy(p->pin, &p->h, sizeof(PlanDev));
+    MHR_CUDA_TRY(cudaMemcpyAsync(p->dregion, p->pin, L.total, cudaMemcpyHostToDevice, st));
+    MHR_CUDA_TRY(cudaEventRecord(p->h2d_done, st));
+    p->h2d_pending = true;
+    MHR_TRY(capture(p, G));
+    MHR_CUDA_TRY(cudaGraphLaunch(p->exec, st));
+    *plan_out = p;
+    return MHR_OK;
+}
+
+static mhr_status read_stats(Plan* p, cudaStream_t st, mhr_stats* stats) {
+    unsigned long long c[kCntCount];
+    MHR_CUDA_TRY(cudaMemcpyAsync(c, p->h.counters, sizeof c, cudaMemcpyDeviceToHost, st));
+    MHR_CUDA_TRY(cudaStreamSynchronize(st));
+    stats->edges_scanned = static_cast<int64_t>(c[kCntScanned]);
+    stats->hits = static_cast<int64_t>(c[kCntHits]);
+    stats->candidates = static_cast<int64_t>(c[kCntCands]);
+    stats->rescored = static_cast<int64_t>(c[kCntRescored]);
+    stats->pruned_edges = static_cast<int64_t>(c[kCntPruned]);
+    stats->dense_queries = static_cast<int64_t>(c[kCntDense]);
+    return MHR_OK;
+}
+
+}  // namespace mhr
+
+using namespace mhr;
+
+extern "C" mhr_status mhr_topk_paths_batched(const mhr_graph* gc, int32_t nq, const uint32_t* s,
+                                             const uint32_t* t, int32_t K, mhr_path* out, int32_t* n_out,
+                                             mhr_mem mem, const mhr_query_opts* opts, mhr_stats* stats,
+                                             void* cuda_stream) {
+    MHR_TRY(check_graph(gc));
+    mhr_graph* G = const_cast<mhr_graph*>(gc);
+    if (nq < 0) return fail(MHR_EINVAL, "nq must be >= 0");
+    if (K < 1) return fail(MHR_EINVAL, "K must be >= 1");
+    if (K > MHR_K_MAX) return fail(MHR_ERANGE, "K exceeds MHR_K_MAX");
+    if (mem != MHR_MEM_HOST && mem != MHR_MEM_DEVICE) return fail(MHR_EINVAL, "unknown mem kind");
+    if (nq == 0) {
+        if (stats) *stats = mhr_stats{};
+        return MHR_OK;
+    }
+    if (!s || !t || !out || !n_out) return fail(MHR_EINVAL, "a required pointer is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<uint32_t> hs, ht;
+    const uint32_t *ps = s, *pt = t;
+    if (mem == MHR_MEM_DEVICE) {
+        hs.resize(nq);
+        ht.resize(nq);
+        MHR_CUDA_TRY(cudaMemcpyAsync(hs.data(), s, sizeof(uint32_t) * nq, cudaMemcpyDeviceToHost, st));
+        MHR_CUDA_TRY(cudaMemcpyAsync(ht.data(), t, sizeof(uint32_t) * nq, cudaMemcpyDeviceToHost, st));
+        MHR_CUDA_TRY(cudaStreamSynchronize(st));
+        ps = hs.data();
+        pt = ht.data();
+    }
+    Plan* p = nullptr;
+    MHR_TRY(run_batch(G, nq, ps, pt, K, opts, st, &p));
+    const cudaMemcpyKind kind = mem == MHR_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    MHR_CUDA_TRY(cudaMemcpyAsync(out, p->h.out, sizeof(mhr_path) * static_cast<size_t>(nq) * K, kind, st));
+    MHR_CUDA_TRY(cudaMemcpyAsync(n_out, p->h.n_out, sizeof(int32_t) * nq, kind, st));
+    if (mem == MHR_MEM_HOST) MHR_CUDA_TRY(cudaStreamSynchronize(st));
+    if (stats) {
+        *stats = mhr_stats{};
+        MHR_TRY(read_stats(p, st, stats));
+    }
+    return MHR_OK;
+}
+
+extern "C" mhr_status mhr_topk_paths(const mhr_graph* g, uint32_t s, uint32_t t, int32_t K, mhr_path* out,
+                                     int32_t* n_out, const mhr_query_opts* opts, mhr_stats* stats) {
+    MHR_TRY(check_graph(g));
+    if (!out || !n_out) return fail(MHR_EINVAL, "out and n_out are required");
+    if (s >= g->dg.n || t >= g->dg.n) return fail(MHR_EINVAL, "s or t is out of range");
+    if (s == t) return fail(MHR_EINVAL, "s == t");
+    if (K < 1) return fail(MHR_EINVAL, "K must be >= 1");
+    if (K > MHR_K_MAX) return fail(MHR_ERANGE, "K exceeds MHR_K_MAX");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, 0);
+    std::vector<mhr_path> buf(K);
+    int32_t n = 0;
+    mhr_status rc = mhr_topk_paths_batched(g, 1, &s, &t, K, buf.data(), &n, MHR_MEM_HOST, opts, stats, nullptr);
+    cudaEventRecord(e1, 0);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != MHR_OK) return rc;
+    std::memcpy(out, buf.data(), sizeof(mhr_path) * std::max(0, n));
+    *n_out = n;
+    if (stats) stats->ms = ms;
+    return MHR_OK;
+}

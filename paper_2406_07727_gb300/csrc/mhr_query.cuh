@@ -1,0 +1,105 @@
+// Data layout of the batched query engine (device side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mhr_internal.cuh"
+
+namespace mhr {
+
+constexpr int kMidThreads = 1024;               // middle-join block (one per SM)
+constexpr int kMidWarps = kMidThreads / 32;
+constexpr int kMaxChunk = 16384;                // edges per work item, upper limit
+constexpr int kDefaultChunk = 16384;
+constexpr int kCandCap = 4096;                  // per-CTA fp32 candidate buffer
+constexpr int kDenseLimit = kCandCap / 2;       // band denser than this -> exact path
+constexpr int kMaxBmWords = 32768;              // shared-memory bitmap: 2^20 vertices
+constexpr int kRankWords = 8;                   // one rank entry per 256 bitmap bits
+constexpr int kMaxRank = kMaxBmWords / kRankWords;
+constexpr int kUnroll = 8;                      // 32-edge groups in flight per warp
+
+// fp32 candidate: one path, identified by its hop-1 entry (index into the CSR
+// row of s), its hop-3 entry (index into the reverse CSR row of t) and r2.
+struct Cand {
+    float s32;
+    uint32_t a_idx;
+    uint32_t c_idx;
+    uint16_t r2;
+    uint16_t pad;
+};
+static_assert(sizeof(Cand) == 16, "Cand is 16 bytes");
+
+// middle edge joining a near-side entry to a far-side entry
+struct Hit {
+    uint32_t near_k;
+    uint32_t far_k;
+    uint32_t epos;  // CSR position of the middle edge (relation id lookup)
+};
+
+// one distinct frontier vertex of a query
+struct ListEnt {
+    uint32_t vertex;
+    uint32_t run_start;  // first entry in the hop-1 row of s (or hop-3 row of t)
+    uint32_t run_len;    // number of parallel edges (relations) to this vertex
+    float maxw;          // max fp32 weight over the run
+    uint32_t deg;        // scan degree: out-degree (hop-1 side) / in-degree (hop-3 side)
+    uint32_t rowstart;   // first CSR (or reverse CSR) position of that scan row
+};
+static_assert(sizeof(ListEnt) == 24, "ListEnt is 24 bytes");
+
+enum {
+    kCntItem = 0,
+    kCntScanned = 1,
+    kCntHits = 2,
+    kCntCands = 3,
+    kCntRescored = 4,
+    kCntDense = 5,
+    kCntPruned = 6,
+    kCntCount = 8
+};
+
+// Everything a batch needs, in device memory; kernels take a pointer to it so
+// a captured CUDA graph keeps working when buffers are regrown between calls.
+struct PlanDev {
+    int32_t nq, K, chunk, sigma;
+    int32_t nbw, pq, band_cap, pad0;
+    int64_t X;     // slots = totA + totC
+    int64_t totA;  // slots of the hop-1 side
+    double err_path;
+    // per-call inputs
+    const uint32_t* S;
+    const uint32_t* T;
+    const int64_t* a_off;  // [nq+1] hop-1 slot offsets (entries of row s)
+    const int64_t* c_off;  // [nq+1] hop-3 slot offsets (entries of reverse row t)
+    // slot arrays [X] (+1 for scans)
+    float* w32;
+    uint32_t* flag;
+    int64_t* scan1;
+    ListEnt* list;
+    uint32_t* degv;
+    int64_t* scan2;
+    uint2* nearP;  // (prefix of scan degree within the query, row start)
+    // per query [nq] (+1 for item_off)
+    int32_t* status;
+    int32_t* dir;       // 1 = forward (scan out-rows of hop-1 vertices), 0 = backward
+    int32_t* near_cnt;
+    int32_t* far_cnt;
+    int64_t* s_near;
+    int64_t* item_off;
+    uint32_t* thr_g;    // order-preserving key of the best known K-th fp32 score
+    int32_t* dense;
+    int32_t* pool_cnt;
+    int32_t* band_cnt;
+    // buffers
+    Hit* hits;          // [grid x kMaxChunk]
+    Cand* pool;         // [nq x pq]
+    Cand* band_cand;    // [nq x band_cap]
+    mhr_path* band_path;// [nq x band_cap]
+    mhr_path* out;      // [nq x K]
+    int32_t* n_out;     // [nq]
+    unsigned long long* counters;  // kCntCount
+    int64_t* partials;             // scan scratch
+};
+
+}  // namespace mhr

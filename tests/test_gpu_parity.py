@@ -1,0 +1,292 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Bar: path ids and order bit-exact; scores bit-exact (the fp64 rescoring
+repeats the oracle's operation order), and in any case within 1e-5 relative.
+Edge scores: fp64 precision bit-exact; fp32 precision within the proven bound.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests._graphs import kg_from_golden, load_golden, path_tuples, random_kg
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def mhr():
+    import paper_2406_07727_gb300 as m
+    return m
+
+
+def compare_query(got, n_got, want, ctx=""):
+    assert n_got == len(want), (ctx, n_got, len(want))
+    g = path_tuples(got[:n_got])
+    w = path_tuples(want)
+    ids_g = [p[1:] for p in g]
+    ids_w = [p[1:] for p in w]
+    assert ids_g == ids_w, (ctx, next(i for i in range(len(ids_g)) if ids_g[i] != ids_w[i]))
+    for a, b in zip(g, w):
+        assert abs(a[0] - b[0]) <= REL_TOL * max(1.0, abs(b[0])), (ctx, a, b)
+    assert [p[0] for p in g] == [p[0] for p in w], (ctx, "scores not bit-identical")
+
+
+def run_and_compare(m, g, S, T, K, fn, opts=None, check=True):
+    G = m.load_kg(g, score_fn=fn)
+    try:
+        out, n_out = m.mhr_topk_paths_batched(G, S, T, K, opts=opts)
+        want, n_want = oracle.topk_paths_batch(g, S, T, K, fn=fn)
+        for q in range(len(S)):
+            if S[q] == T[q] or S[q] >= g.n or T[q] >= g.n:
+                assert n_out[q] == -1
+                continue
+            compare_query(out[q], int(n_out[q]), want[q, : n_want[q]], ctx=(q, int(S[q]), int(T[q])))
+        return out, n_out
+    finally:
+        G.close()
+
+
+# --------------------------------------------------------------------------- edge scores
+@pytest.mark.parametrize("fn", ["transe", "distmult"])
+def test_edge_scores_golden(mhr, fn):
+    gj = load_golden()
+    g = kg_from_golden(gj)
+    G = mhr.load_kg(g, score_fn=fn)
+    rows = gj[f"edge_weights_{fn}"]["rows"]
+    src = np.array([r[0] for r in rows], dtype=np.uint32)
+    rel = np.array([r[1] for r in rows], dtype=np.uint16)
+    dst = np.array([r[2] for r in rows], dtype=np.uint32)
+    want = [r[3] for r in rows]
+    assert mhr.mhr_edge_scores(G, src, rel, dst, precision=2).tolist() == want
+    assert mhr.mhr_edge_scores(G, src, rel, dst, precision=0).astype(np.float64).tolist() == want
+    G.close()
+
+
+@pytest.mark.parametrize("fn", ["transe", "distmult"])
+@pytest.mark.parametrize("dtype,d", [("f32", 5), ("f32", 128), ("bf16", 64), ("bf16", 7), ("f32", 256)])
+def test_edge_scores_random(mhr, fn, dtype, d):
+    rng = np.random.default_rng(d)
+    g = random_kg(rng, 500, 20000, 7, d, dtype=dtype, scale=0.3)
+    G = mhr.load_kg(g, score_fn=fn)
+    w64 = mhr.mhr_edge_scores(G, precision=2)            # all CSR edges
+    w32 = mhr.mhr_edge_scores(G, precision=0)
+    src = g.src_of_edges()
+    want = oracle.edge_weights(g, src, g.rels, g.cols, fn=fn)
+    assert np.array_equal(w64, want)                     # bit-exact
+    # fp32 within the proven per-edge bound (global norms)
+    ve = g.vemb_f32().astype(np.float64)
+    re_ = g.remb_f32().astype(np.float64)
+    if fn == "transe":
+        N = 2 * np.abs(ve).sum(1).max() + np.abs(re_).sum(1).max()
+        bound = (d + 4) * 2.0 ** -24 / (1 - (d + 4) * 2.0 ** -24) * (N + 2)
+    else:
+        M = np.abs(re_).max() * (ve ** 2).sum(1).max()
+        bound = (d + 3) * 2.0 ** -24 / (1 - (d + 3) * 2.0 ** -24) * M
+    assert np.abs(w32.astype(np.float64) - want).max() <= bound
+    # explicit edge list, including a subset
+    idx = rng.choice(g.E, 777, replace=False)
+    sub = mhr.mhr_edge_scores(G, src[idx], g.rels[idx], g.cols[idx], precision=2)
+    assert np.array_equal(sub, want[idx])
+    G.close()
+
+
+# --------------------------------------------------------------------------- golden paths
+@pytest.mark.parametrize("fn", ["transe", "distmult"])
+def test_topk_golden(mhr, fn):
+    gj = load_golden()
+    g = kg_from_golden(gj)
+    G = mhr.load_kg(g, score_fn=fn)
+    want = [tuple(p) for p in gj[f"expected_{fn}"]["paths_score_u_r1_v_r2_r3"]]
+    for K in (1, 3, 5, 11, 20, 1024):
+        got = mhr.mhr_topk_paths(G, 0, 9, K)
+        assert path_tuples(got) == [(float(p[0]),) + tuple(p[1:]) for p in want[:K]]
+    if fn == "transe":
+        want2 = [tuple(p) for p in gj["expected2_transe"]["paths_score_u_r1_v_r2_r3"]]
+        got = mhr.mhr_topk_paths(G, 3, 9, 10)
+        assert path_tuples(got) == [(float(p[0]),) + tuple(p[1:]) for p in want2]
+    G.close()
+
+
+def test_topk_golden_batched_and_edge_cases(mhr):
+    gj = load_golden()
+    g = kg_from_golden(gj)
+    S = np.array([0, 3, 0, 5, 7, 0, 8], dtype=np.uint32)
+    T = np.array([9, 9, 0, 9, 0, 8, 9], dtype=np.uint32)  # (0,0) invalid; (0,8): no paths
+    run_and_compare(mhr, g, S, T, 4, "transe")
+    G = mhr.load_kg(g)
+    with pytest.raises(mhr.MhrError) as e:
+        mhr.mhr_topk_paths(G, 2, 2, 5)
+    assert e.value.status == mhr.MHR_EINVAL
+    with pytest.raises(mhr.MhrError) as e:
+        mhr.mhr_topk_paths(G, 0, 10, 5)
+    assert e.value.status == mhr.MHR_EINVAL
+    with pytest.raises(mhr.MhrError) as e:
+        mhr.mhr_topk_paths(G, 0, 9, mhr.MHR_K_MAX + 1)
+    assert e.value.status == mhr.MHR_ERANGE
+    with pytest.raises(mhr.MhrError) as e:
+        mhr.mhr_topk_paths(G, 0, 9, 0)
+    assert e.value.status == mhr.MHR_EINVAL
+    assert len(mhr.mhr_topk_paths(G, 0, 8, 5)) == 0
+    G.close()
+
+
+# --------------------------------------------------------------------------- random graphs
+@pytest.mark.parametrize("fn", ["transe", "distmult"])
+def test_topk_random_small_graphs(mhr, fn):
+    rng = np.random.default_rng(101 if fn == "transe" else 202)
+    for trial in range(30):
+        n = int(rng.integers(8, 300))
+        m = int(rng.integers(20, 30 * n))
+        R = int(rng.integers(1, 6))
+        d = int(rng.choice([1, 3, 4, 8, 16, 64]))
+        dtype = "bf16" if trial % 3 == 0 else "f32"
+        g = random_kg(rng, n, m, R, d, dtype=dtype, dyadic=(trial % 5 == 0))
+        nq = 24
+        S = rng.integers(0, n, nq).astype(np.uint32)
+        T = rng.integers(0, n, nq).astype(np.uint32)
+        K = int(rng.choice([1, 2, 7, 50, 300]))
+        run_and_compare(mhr, g, S, T, K, fn)
+
+
+def test_topk_all_ties_zero_embeddings(mhr):
+    """Every score equal: the order is the id order and the fp32 screen cannot
+    separate anything (exercises the tie-heavy exact path)."""
+    rng = np.random.default_rng(7)
+    for trial in range(6):
+        g = random_kg(rng, 200, 8000, 3, 8, zero=True)
+        S = rng.integers(0, 200, 10).astype(np.uint32)
+        T = rng.integers(0, 200, 10).astype(np.uint32)
+        for fn in ("transe", "distmult"):
+            run_and_compare(mhr, g, S, T, int(rng.choice([5, 64, 500])), fn)
+
+
+def test_topk_dyadic_many_ties_large_K(mhr):
+    rng = np.random.default_rng(8)
+    g = random_kg(rng, 400, 30000, 2, 2, dyadic=True)
+    S = rng.integers(0, 400, 16).astype(np.uint32)
+    T = rng.integers(0, 400, 16).astype(np.uint32)
+    run_and_compare(mhr, g, S, T, 1024, "transe")
+    run_and_compare(mhr, g, S, T, 100, "distmult")
+
+
+@pytest.mark.parametrize("chunk", [32, 64, 1024, 16384])
+def test_topk_chunk_sizes(mhr, chunk):
+    """Work items of any size give the same answer (several items per query,
+    ragged tails, hub rows split across items)."""
+    g = synth.gen_rmat_kg(13, 6000, 120_000, 5, 3, seed=4)
+    g.vemb, g.remb = synth.gen_embeddings(g.n, g.R, 16, 0.25, seed=4)
+    S, T = synth.queries_edge_biased(g, 20, seed=4)
+    run_and_compare(mhr, g, S, T, 60, "transe", opts={"chunk": chunk})
+
+
+def test_tiny_workload(mhr):
+    """10k vertices / 100k edges Zipf(2.1), d=64 fp32, hub query, K=10 (+ K=100)."""
+    g, S, T, K, spec = synth.workload("tiny")
+    run_and_compare(mhr, g, S, T, K, "transe")
+    run_and_compare(mhr, g, S, T, 100, "transe")
+    run_and_compare(mhr, g, S, T, K, "distmult")
+    S2, T2 = synth.queries_edge_biased(g, 64, seed=1)
+    run_and_compare(mhr, g, S2, T2, K, "transe")
+
+
+def test_both_directions_and_repeat_determinism(mhr):
+    g = synth.gen_rmat_kg(14, 12000, 200_000, 8, 3, seed=5)
+    g.vemb, g.remb = synth.gen_embeddings(g.n, g.R, 32, 1 / math.sqrt(32), seed=5)
+    od, idg = g.out_degree(), g.in_degree()
+    rng = np.random.default_rng(5)
+    # hub source with low in-degree target and the reverse, so both scan sides run
+    hubs = np.argsort(-od)[:8].astype(np.uint32)
+    lows = np.flatnonzero((idg > 0) & (idg < 3))[:8].astype(np.uint32)
+    S = np.concatenate([hubs, lows, rng.integers(0, g.n, 16).astype(np.uint32)])
+    T = np.concatenate([lows, hubs, rng.integers(0, g.n, 16).astype(np.uint32)])
+    out1, n1 = run_and_compare(mhr, g, S, T, 100, "transe")
+    G = mhr.load_kg(g)
+    out2, n2 = mhr.mhr_topk_paths_batched(G, S, T, 100)
+    G.close()
+    assert np.array_equal(n1, n2)
+    for q in range(len(S)):
+        assert out1[q][: n1[q]].tobytes() == out2[q][: n2[q]].tobytes()
+
+
+def test_large_vertex_count_coarse_bitmap(mhr):
+    """n > 2^20: the shared-memory membership bitmap becomes coarse and
+    positives are confirmed by binary search."""
+    g = synth.gen_rmat_kg(22, 3_000_000, 2_000_000, 4, 2, seed=6)
+    g.vemb, g.remb = synth.gen_embeddings(g.n, g.R, 8, 0.3, seed=6)
+    S, T = synth.queries_edge_biased(g, 24, seed=6)
+    run_and_compare(mhr, g, S, T, 50, "transe")
+
+
+def test_device_memory_batched(mhr):
+    torch = pytest.importorskip("torch")
+    g, S, T, K, spec = synth.workload("tiny")
+    S2, T2 = synth.queries_edge_biased(g, 32, seed=2)
+    G = mhr.load_kg(g, device=True)
+    dS, dT = torch.from_numpy(S2.astype(np.int32)).cuda(), torch.from_numpy(T2.astype(np.int32)).cuda()
+    out, n_out = mhr.mhr_topk_paths_batched(G, dS, dT, 20, stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    paths = mhr.paths_from_device(out, 20)
+    n_out = n_out.cpu().numpy()
+    want, n_want = oracle.topk_paths_batch(g, S2, T2, 20)
+    for q in range(len(S2)):
+        compare_query(paths[q], int(n_out[q]), want[q, : n_want[q]], ctx=q)
+    G.close()
+
+
+def test_invalid_graphs_rejected(mhr):
+    gj = load_golden()
+    g = kg_from_golden(gj)
+    bad = dict(offsets=g.offsets, cols=g.cols, rels=g.rels, vertex_emb=g.vemb, rel_emb=g.remb)
+
+    def load(**kw):
+        a = dict(bad)
+        a.update(kw)
+        return mhr.mhr_graph_load(a["offsets"], a["cols"], a["rels"], a["vertex_emb"], a["rel_emb"], g.R)
+
+    cols = g.cols.copy()
+    cols[0] = 99
+    with pytest.raises(mhr.MhrError, match="destination"):
+        load(cols=cols)
+    rels = g.rels.copy()
+    rels[0] = 7
+    with pytest.raises(mhr.MhrError, match="relation"):
+        load(rels=rels)
+    cols = g.cols.copy()
+    cols[1] = cols[0]
+    rels = g.rels.copy()
+    rels[1] = rels[0]
+    with pytest.raises(mhr.MhrError, match="sorted"):
+        load(cols=cols, rels=rels)
+    cols = g.cols.copy()
+    cols[0] = 0  # row 0 edge to itself
+    with pytest.raises(mhr.MhrError):
+        load(cols=cols)
+    ve = g.vemb.copy()
+    ve[3, 1] = np.nan
+    with pytest.raises(mhr.MhrError, match="NaN"):
+        load(vertex_emb=ve)
+    off = g.offsets.copy()
+    off[3], off[4] = off[4], off[3]
+    with pytest.raises(mhr.MhrError, match="offsets"):
+        load(offsets=off)
+
+
+@pytest.mark.slow
+def test_medium_workload_sampled(mhr):
+    """The benchmark workload (R-MAT 1M vertices, 20M edges, d=128 fp32,
+    64 edge-biased queries, K=100) in the benchmark's launch configuration;
+    the oracle recomputes a sample of 12 queries."""
+    g, S, T, K, spec = synth.workload("medium")
+    G = mhr.load_kg(g)
+    out, n_out = mhr.mhr_topk_paths_batched(G, S, T, K)
+    G.close()
+    sample = np.arange(0, len(S), max(1, len(S) // 12))[:12]
+    want, n_want = oracle.topk_paths_batch(g, S[sample], T[sample], K)
+    for i, q in enumerate(sample):
+        compare_query(out[q], int(n_out[q]), want[i, : n_want[i]], ctx=int(q))
