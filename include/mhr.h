@@ -113,11 +113,14 @@ typedef struct {
 typedef struct {
     int64_t edges_scanned; /* middle-join CSR entries streamed */
     int64_t hits;          /* middle edges that joined both frontiers */
+    int64_t paths;         /* simple s->t three-hop paths enumerated (scored) */
     int64_t candidates;    /* fp32 candidates kept for the final merge */
     int64_t rescored;      /* candidates rescored in fp64 */
     int64_t pruned_edges;  /* middle edges skipped by provable bounds */
     int64_t dense_queries; /* queries resolved by the exact (tie-heavy) path */
     double ms;             /* wall time of the call (synchronous calls only) */
+    double ms_device;      /* device time of the whole launch sequence (CUDA events) */
+    double ms_join;        /* device time of the middle-join kernel (CUDA events) */
 } mhr_stats;
 
 /*

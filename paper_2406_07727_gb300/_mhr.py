@@ -57,9 +57,10 @@ class QueryOpts(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("edges_scanned", ctypes.c_int64), ("hits", ctypes.c_int64),
-                ("candidates", ctypes.c_int64), ("rescored", ctypes.c_int64),
+                ("paths", ctypes.c_int64), ("candidates", ctypes.c_int64), ("rescored", ctypes.c_int64),
                 ("pruned_edges", ctypes.c_int64), ("dense_queries", ctypes.c_int64),
-                ("ms", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("ms_device", ctypes.c_double),
+                ("ms_join", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

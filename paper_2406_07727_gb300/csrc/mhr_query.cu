@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
     const double two_err = 2.0 * P->err_path;
     const int64_t total_items = P->item_off[nq];
     Hit* hits = P->hits + static_cast<int64_t>(blockIdx.x) * kMaxChunk;
-    unsigned long long n_scanned = 0, n_hits = 0, n_cands = 0;
+    unsigned long long n_scanned = 0, n_hits = 0, n_cands = 0, n_paths_w = 0;
     int cur_q = -1;
     if (threadIdx.x == 0) sm.q = -1;
 
@@ -690,6 +690,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                         slice = 0;
                         const float smax = __fadd_rn(__fadd_rn(ea.maxw, w2), ec.maxw);
                         if (smax < thr) {
+                            if (lane == 0) n_paths_w += ea.run_len * ec.run_len;
                             h += kMidWarps;
                             have_w2 = false;
                             continue;
@@ -697,6 +698,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                     }
                     const uint32_t na = ea.run_len, nc = ec.run_len;
                     const uint32_t total = na * nc;
+                    if (slice == 0 && lane == 0) n_paths_w += total;
                     bool stop = false;
                     while (slice < total) {
                         const uint32_t c = slice + lane;
@@ -749,6 +751,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         atomicAdd(&P->counters[kCntHits], n_hits);
         atomicAdd(&P->counters[kCntCands], n_cands);
     }
+    if (lane == 0 && n_paths_w) atomicAdd(&P->counters[kCntPaths], n_paths_w);
 }
 
 // ===========================================================================
@@ -1021,14 +1024,24 @@ struct Plan {
     std::vector<void*> fixed;
     void* slot_mem = nullptr;
     int64_t slot_cap = 0;
-    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
     cudaStream_t cap = nullptr;
     cudaEvent_t h2d_done = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // before / join / after / end
     bool h2d_pending = false;
+    void drop_graphs() {
+        for (cudaGraphExec_t& x : exec)
+            if (x) {
+                cudaGraphExecDestroy(x);
+                x = nullptr;
+            }
+    }
     ~Plan() {
-        if (exec) cudaGraphExecDestroy(exec);
+        drop_graphs();
         if (cap) cudaStreamDestroy(cap);
         if (h2d_done) cudaEventDestroy(h2d_done);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
         for (void* p : fixed) cudaFree(p);
         if (slot_mem) cudaFree(slot_mem);
         if (dregion) cudaFree(dregion);
@@ -1118,50 +1131,68 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
     p->h.list = reinterpret_cast<ListEnt*>(b + o_list);
     p->h.nearP = reinterpret_cast<uint2*>(b + o_near);
     // scan kernels take raw pointers, so a new buffer needs a new capture
-    if (p->exec) {
-        cudaGraphExecDestroy(p->exec);
-        p->exec = nullptr;
-    }
+    p->drop_graphs();
     return MHR_OK;
 }
 
-static cudaError_t launch_sequence(Plan* p, const mhr_graph* G, cudaStream_t st) {
+// The sequence is captured as three graphs (before, the join, after) so that
+// timing events recorded between their launches on the caller's stream bracket
+// the join kernel exactly.
+static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int part) {
     const PlanDev* d = reinterpret_cast<const PlanDev*>(p->dregion);
     const int sms = std::max(1, G->num_sms);
     const DevGraph& g = G->dg;
     const int64_t* nX = reinterpret_cast<const int64_t*>(p->dregion + offsetof(PlanDev, X));
-    k_init<<<std::max(1, std::min(sms, (p->nq + 255) / 256)), 256, 0, st>>>(d, g);
-    k_expand<<<sms * 8, 256, 0, st>>>(d, g);
-    cudaError_t e = device_excl_scan<uint32_t>(p->h.flag, nX, p->h.partials, p->h.scan1, st);
-    if (e != cudaSuccess) return e;
-    k_lists<<<sms * 4, 256, 0, st>>>(d, g);
-    e = device_excl_scan<uint32_t>(p->h.degv, nX, p->h.partials, p->h.scan2, st);
-    if (e != cudaSuccess) return e;
-    k_plan<<<1, 1024, 0, st>>>(d);
-    k_near<<<sms * 4, 256, 0, st>>>(d);
-    k_middle<kUnroll><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
-    k_merge1<<<std::min(p->nq, sms * 2), 1024, 0, st>>>(d);
-    k_rescore<<<sms * 4, 128, 0, st>>>(d, g);
-    k_merge2<<<std::min(p->nq, sms * 2), 1024, merge2_smem_bytes(p->h.band_cap), st>>>(d);
-    k_exact<<<std::min(p->nq, sms * 2), 1024, exact_smem_bytes(), st>>>(d, g);
+    if (part == 0) {
+        k_init<<<std::max(1, std::min(sms, (p->nq + 255) / 256)), 256, 0, st>>>(d, g);
+        k_expand<<<sms * 8, 256, 0, st>>>(d, g);
+        cudaError_t e = device_excl_scan<uint32_t>(p->h.flag, nX, p->h.partials, p->h.scan1, st);
+        if (e != cudaSuccess) return e;
+        k_lists<<<sms * 4, 256, 0, st>>>(d, g);
+        e = device_excl_scan<uint32_t>(p->h.degv, nX, p->h.partials, p->h.scan2, st);
+        if (e != cudaSuccess) return e;
+        k_plan<<<1, 1024, 0, st>>>(d);
+        k_near<<<sms * 4, 256, 0, st>>>(d);
+    } else if (part == 1) {
+        k_middle<kUnroll><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
+    } else {
+        k_merge1<<<std::min(p->nq, sms * 2), 1024, 0, st>>>(d);
+        k_rescore<<<sms * 4, 128, 0, st>>>(d, g);
+        k_merge2<<<std::min(p->nq, sms * 2), 1024, merge2_smem_bytes(p->h.band_cap), st>>>(d);
+        k_exact<<<std::min(p->nq, sms * 2), 1024, exact_smem_bytes(), st>>>(d, g);
+    }
     return cudaGetLastError();
 }
 
 static mhr_status capture(Plan* p, const mhr_graph* G) {
-    if (p->exec) return MHR_OK;
-    cudaGraph_t graph = nullptr;
-    MHR_CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = launch_sequence(p, G, p->cap);
-    cudaError_t e2 = cudaStreamEndCapture(p->cap, &graph);
-    if (e != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        return cuda_fail(e, "kernel launch during capture");
+    if (p->exec[0]) return MHR_OK;
+    for (int part = 0; part < 3; ++part) {
+        cudaGraph_t graph = nullptr;
+        MHR_CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = launch_part(p, G, p->cap, part);
+        cudaError_t e2 = cudaStreamEndCapture(p->cap, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            p->drop_graphs();
+            return cuda_fail(e != cudaSuccess ? e : e2, "kernel launch during capture");
+        }
+        e = cudaGraphInstantiate(&p->exec[part], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            p->drop_graphs();
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
     }
-    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&p->exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     return MHR_OK;
+}
+
+static cudaError_t launch_graphs(Plan* p, cudaStream_t st) {
+    cudaError_t e;
+    for (int part = 0; part < 3; ++part) {
+        if ((e = cudaEventRecord(p->ev[part], st)) != cudaSuccess) return e;
+        if ((e = cudaGraphLaunch(p->exec[part], st)) != cudaSuccess) return e;
+    }
+    return cudaEventRecord(p->ev[3], st);
 }
 
 static int choose_sigma(int64_t n) {
@@ -1222,6 +1253,10 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) 
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
     e = cudaEventCreateWithFlags(&p->h2d_done, cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+    for (cudaEvent_t& ev : p->ev) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+    }
     e = cudaFuncSetAttribute(k_middle<kUnroll>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(mid_smem_bytes()));
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaFuncSetAttribute (middle join)"));
@@ -1295,7 +1330,7 @@ static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint
     MHR_CUDA_TRY(cudaEventRecord(p->h2d_done, st));
     p->h2d_pending = true;
     MHR_TRY(capture(p, G));
-    MHR_CUDA_TRY(cudaGraphLaunch(p->exec, st));
+    MHR_CUDA_TRY(launch_graphs(p, st));
     *plan_out = p;
     return MHR_OK;
 }
@@ -1306,10 +1341,18 @@ static mhr_status read_stats(Plan* p, cudaStream_t st, mhr_stats* stats) {
     MHR_CUDA_TRY(cudaStreamSynchronize(st));
     stats->edges_scanned = static_cast<int64_t>(c[kCntScanned]);
     stats->hits = static_cast<int64_t>(c[kCntHits]);
+    stats->paths = static_cast<int64_t>(c[kCntPaths]);
     stats->candidates = static_cast<int64_t>(c[kCntCands]);
     stats->rescored = static_cast<int64_t>(c[kCntRescored]);
     stats->pruned_edges = static_cast<int64_t>(c[kCntPruned]);
     stats->dense_queries = static_cast<int64_t>(c[kCntDense]);
+    float a = -1.f, b = -1.f;
+    if (cudaEventElapsedTime(&a, p->ev[0], p->ev[3]) != cudaSuccess) a = -1.f;
+    // ev[1] .. ev[2] bracket the join graph
+    if (cudaEventElapsedTime(&b, p->ev[1], p->ev[2]) != cudaSuccess) b = -1.f;
+    cudaGetLastError();
+    stats->ms_device = a;
+    stats->ms_join = b;
     return MHR_OK;
 }
 

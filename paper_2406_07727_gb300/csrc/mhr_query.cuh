@@ -56,6 +56,7 @@ enum {
     kCntRescored = 4,
     kCntDense = 5,
     kCntPruned = 6,
+    kCntPaths = 7,
     kCntCount = 8
 };
 

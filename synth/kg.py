@@ -320,10 +320,43 @@ WORKLOADS = {
 }
 
 
+def _cache_path(name, seed, spec):
+    import hashlib
+    import json
+    import os
+    d = os.environ.get("MHR_SYNTH_CACHE")
+    if not d:
+        return None
+    key = hashlib.sha1(json.dumps([name, seed, sorted(spec.items())], default=str).encode()).hexdigest()[:16]
+    os.makedirs(d, exist_ok=True)
+    return os.path.join(d, f"{name}-{key}.npz")
+
+
 def workload(name: str, seed: int = 0, **override):
-    """Build a named workload.  Returns (KG with embeddings, S, T, K, spec)."""
+    """Build a named workload.  Returns (KG with embeddings, S, T, K, spec).
+    Set MHR_SYNTH_CACHE to a directory to reuse generated arrays."""
     spec = dict(WORKLOADS[name])
     spec.update(override)
+    cp = _cache_path(name, seed, spec)
+    if cp is not None:
+        import os
+        if os.path.exists(cp):
+            z = np.load(cp)
+            g = KG(n=spec["n"], R=spec["R"], n_types=spec["n_types"], offsets=z["offsets"],
+                   cols=z["cols"], rels=z["rels"], vtypes=z["vtypes"], vemb=z["vemb"],
+                   remb=z["remb"], dtype=spec["dtype"])
+            return g, z["S"], z["T"], spec["K"], spec
+    g, S, T, K, spec = _build_workload(spec, seed)
+    if cp is not None:
+        tmp = cp + ".tmp.npz"
+        np.savez(tmp, offsets=g.offsets, cols=g.cols, rels=g.rels, vtypes=g.vtypes, vemb=g.vemb,
+                 remb=g.remb, S=S, T=T)
+        import os
+        os.replace(tmp, cp)
+    return g, S, T, K, spec
+
+
+def _build_workload(spec, seed):
     if spec["kind"] == "zipf":
         g = gen_zipf_kg(spec["n"], spec["E"], spec["R"], spec["n_types"], seed=seed)
     else:

@@ -43,7 +43,7 @@ def test_struct_layouts():
     assert m.PATH_DTYPE.itemsize == 24
     assert ctypes.sizeof(_mhr.GraphDesc) == 104
     assert ctypes.sizeof(_mhr.QueryOpts) == 32
-    assert ctypes.sizeof(_mhr.Stats) == 56
+    assert ctypes.sizeof(_mhr.Stats) == 80
 
 
 def test_host_side_argument_checks():

@@ -41,12 +41,14 @@ def run_and_compare(m, g, S, T, K, fn, opts=None, check=True):
     G = m.load_kg(g, score_fn=fn)
     try:
         out, n_out = m.mhr_topk_paths_batched(G, S, T, K, opts=opts)
-        want, n_want = oracle.topk_paths_batch(g, S, T, K, fn=fn)
-        for q in range(len(S)):
-            if S[q] == T[q] or S[q] >= g.n or T[q] >= g.n:
-                assert n_out[q] == -1
-                continue
-            compare_query(out[q], int(n_out[q]), want[q, : n_want[q]], ctx=(q, int(S[q]), int(T[q])))
+        valid = (S != T) & (S < g.n) & (T < g.n)
+        assert (n_out[~valid] == -1).all()
+        if not check:
+            return out, n_out
+        vi = np.flatnonzero(valid)
+        want, n_want = oracle.topk_paths_batch(g, S[vi], T[vi], K, fn=fn)
+        for i, q in enumerate(vi):
+            compare_query(out[q], int(n_out[q]), want[i, : n_want[i]], ctx=(int(q), int(S[q]), int(T[q])))
         return out, n_out
     finally:
         G.close()
