@@ -223,9 +223,11 @@ def run_gpu(args):
     n_out = torch.empty(nq, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
+    opts = {"chunk": args.chunk} if args.chunk else None
+
     def step(with_stats=False):
         return mhr.mhr_topk_paths_batched(G, dS, dT, K, out=out, n_out=n_out, stream=stream,
-                                          with_stats=with_stats)
+                                          opts=opts, with_stats=with_stats)
 
     for _ in range(args.warmup):
         step()
@@ -264,7 +266,7 @@ def run_gpu(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h_out, h_n = mhr.mhr_topk_paths_batched(G, S, T, K)
+        h_out, h_n = mhr.mhr_topk_paths_batched(G, S, T, K, opts=opts)
         e2e_times.append(time.perf_counter() - t0)
     e2e_t = torch.tensor([sum(e2e_times)], dtype=torch.float64, device="cuda")
     if ws > 1:
@@ -332,6 +334,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--chunk", type=int, default=0, help="middle-join work item size (0 = default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

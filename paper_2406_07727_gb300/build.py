@@ -20,6 +20,8 @@ LIB = os.path.join(OUT_DIR, "libmhr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-I" + os.path.join(ROOT, "include"), "--resource-usage"] + ARCH
+# extra flags for instrumented builds, e.g. MHR_NVCC_EXTRA="-DMHR_PHASE_TIMING"
+EXTRA = os.environ.get("MHR_NVCC_EXTRA", "").split()
 
 
 def _nvcc() -> str:
@@ -38,7 +40,7 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or EXTRA:
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
@@ -53,7 +55,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, "-c", src, "-o", obj] + NVCC_FLAGS
+        cmd = [nvcc, "-c", src, "-o", obj] + NVCC_FLAGS + EXTRA
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -176,43 +176,55 @@ __global__ void k_init(const PlanDev* __restrict__ P, DevGraph g) {
         P->n_out[q] = 0;
     }
     if (tid < kCntCount) P->counters[tid] = 0ull;
+    for (int c = tid; c < P->grid; c += gridDim.x * blockDim.x) P->cursors[c] = 0ull;
 }
 
-// one warp per slot: fp32 weight, exclusion, run-head flag
+// one group of G lanes per slot: fp32 weight, exclusion, run-head flag
 __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, DevGraph g) {
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
-    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const int G = P->score_width;
+    const int sub = lane & (G - 1);
+    const int64_t group = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / G;
+    const int64_t ngroups = (static_cast<int64_t>(gridDim.x) * blockDim.x) / G;
     const int64_t X = P->X, totA = P->totA;
     const int nq = P->nq;
-    for (int64_t x = warp; x < X; x += nwarps) {
-        const bool sideA = x < totA;
-        const int64_t lx = sideA ? x : x - totA;
-        const int64_t* offs = sideA ? P->a_off : P->c_off;
-        const int q = static_cast<int>(upper_bound_i64(offs, nq + 1, lx) - 1);
-        const int64_t k = lx - offs[q];
-        const uint32_t s = P->S[q], t = P->T[q];
-        uint32_t vtx, r, prev = 0xffffffffu;
-        uint32_t sdeg;
-        if (sideA) {
-            const int64_t p = g.off[s] + k;
-            vtx = g.col[p];
-            r = g.rel[p];
-            if (k > 0) prev = g.col[p - 1];
-            sdeg = static_cast<uint32_t>(g.off[vtx + 1] - g.off[vtx]);
-        } else {
-            const int64_t p = g.roff[t] + k;
-            vtx = g.rcol[p];
-            r = g.rrel[p];
-            if (k > 0) prev = g.rcol[p - 1];
-            sdeg = static_cast<uint32_t>(g.roff[vtx + 1] - g.roff[vtx]);
+    // every lane of a warp runs the same number of iterations (group shuffles)
+    const int64_t iters = (X + ngroups - 1) / ngroups;
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t x = group + it * ngroups;
+        const bool live = x < X;
+        uint32_t s = 0, t = 0, vtx = 0, r = 0, prev = 0xffffffffu, sdeg = 0;
+        int64_t k = 0;
+        bool sideA = true;
+        if (live) {
+            sideA = x < totA;
+            const int64_t lx = sideA ? x : x - totA;
+            const int64_t* offs = sideA ? P->a_off : P->c_off;
+            const int q = static_cast<int>(upper_bound_i64(offs, nq + 1, lx) - 1);
+            k = lx - offs[q];
+            s = P->S[q];
+            t = P->T[q];
+            if (sideA) {
+                const int64_t p = g.off[s] + k;
+                vtx = g.col[p];
+                r = g.rel[p];
+                if (k > 0) prev = g.col[p - 1];
+                sdeg = static_cast<uint32_t>(g.off[vtx + 1] - g.off[vtx]);
+            } else {
+                const int64_t p = g.roff[t] + k;
+                vtx = g.rcol[p];
+                r = g.rrel[p];
+                if (k > 0) prev = g.rcol[p - 1];
+                sdeg = static_cast<uint32_t>(g.roff[vtx + 1] - g.roff[vtx]);
+            }
         }
-        const bool excl = (vtx == s) || (vtx == t);
-        const float w = sideA ? edge_w32_group(g, s, r, vtx, lane, 32) : edge_w32_group(g, vtx, r, t, lane, 32);
-        // A vertex with no scan edges can neither be scanned nor be hit, so it
-        // never lies on a path: it is dropped from the distinct list.
-        const bool head = !excl && sdeg > 0 && (k == 0 || prev != vtx);
-        if (lane == 0) {
+        const uint32_t hu = sideA ? s : vtx, tv = sideA ? vtx : t;
+        const float w = edge_w32_group(g, hu, r, tv, sub, G);
+        if (live && sub == 0) {
+            const bool excl = (vtx == s) || (vtx == t);
+            // A vertex with no scan edges can neither be scanned nor be hit, so it
+            // never lies on a path: it is dropped from the distinct list.
+            const bool head = !excl && sdeg > 0 && (k == 0 || prev != vtx);
             P->w32[x] = excl ? neg_inf() : w;
             P->flag[x] = head ? 1u : 0u;
             P->degv[x] = 0u;
@@ -475,12 +487,50 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
     const int64_t total_items = P->item_off[nq];
     Hit* hits = P->hits + static_cast<int64_t>(blockIdx.x) * kMaxChunk;
     unsigned long long n_scanned = 0, n_hits = 0, n_cands = 0, n_paths_w = 0;
+#ifdef MHR_PHASE_TIMING
+    // cycles per phase, thread 0: 0 fetch + query switch, 1 item setup, 2 scan, 3 score
+    unsigned long long ph[4] = {0, 0, 0, 0};
+    unsigned long long tph = clock64();
+#define MHR_PHASE(i)                                  \
+    do {                                              \
+        if (threadIdx.x == 0) {                       \
+            const unsigned long long now__ = clock64(); \
+            ph[i] += now__ - tph;                     \
+            tph = now__;                              \
+        }                                             \
+    } while (0)
+#else
+#define MHR_PHASE(i) \
+    do {             \
+    } while (0)
+#endif
     int cur_q = -1;
+    int victim = 0;  // thread 0: offset of the range it currently drains
     if (threadIdx.x == 0) sm.q = -1;
 
     for (;;) {
         if (threadIdx.x == 0) {
-            const int64_t it = static_cast<int64_t>(atomicAdd(&P->counters[kCntItem], 1ull));
+            // Items are laid out query by query; CTA b owns the contiguous range
+            // [b*N/grid, (b+1)*N/grid) so it meets few queries, then steals from
+            // the following ranges once its own is drained.
+            int64_t it = total_items;
+            while (victim < static_cast<int>(gridDim.x)) {
+                // every item taken already: stop probing the other ranges
+                if (victim > 0 && atomicAdd(&P->counters[kCntItem], 0ull) >= static_cast<unsigned long long>(total_items))
+                    break;
+                const int v = (blockIdx.x + victim) % gridDim.x;
+                const int64_t lo = total_items * v / gridDim.x;
+                const int64_t hi = total_items * (v + 1) / gridDim.x;
+                if (lo < hi) {
+                    const int64_t idx = static_cast<int64_t>(atomicAdd(&P->cursors[v], 1ull));
+                    if (lo + idx < hi) {
+                        it = lo + idx;
+                        atomicAdd(&P->counters[kCntItem], 1ull);
+                        break;
+                    }
+                }
+                ++victim;
+            }
             sm.item = it;
             if (it < total_items) {
                 const int q = static_cast<int>(upper_bound_i64(P->item_off, nq + 1, it) - 1);
@@ -497,8 +547,14 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
             setup_query(sm, P, q);
             cur_q = q;
         }
+        MHR_PHASE(0);
         if (threadIdx.x == 0) {
             sm.skip = sm.local_dense || atomicOr(&P->dense[q], 0) != 0;
+            const uint32_t gk = atomicOr(&P->thr_g[q], 0u);
+            if (gk > sm.lt_key) {
+                sm.lt_key = gk;
+                sm.thr_keep = keep_threshold(gk, two_err);
+            }
             const int64_t e0 = (item - P->item_off[q]) * P->chunk;
             const int64_t e1 = min(e0 + static_cast<int64_t>(P->chunk), sm.s_near);
             sm.e0 = static_cast<uint32_t>(e0);
@@ -563,6 +619,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         }
         __syncthreads();
 
+        MHR_PHASE(1);
         // --- scan: stream near rows, probe the far bitmap, stage hits
         const uint32_t* colsrc = sm.dir ? g.col : g.rcol;
         const ListEnt* far = P->list + sm.far_base;
@@ -656,101 +713,147 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         }
         if (threadIdx.x == 0) sm.round_cnt = sm.cand_cnt;
         __syncthreads();
+        MHR_PHASE(2);
         const int nh = sm.hit_cnt;
         if (threadIdx.x == 0) {
             n_scanned += e1 - e0;
             n_hits += static_cast<unsigned long long>(nh);
         }
 
-        // --- score hits; keep paths that can still reach the top K
+        // --- score hits; keep paths that can still reach the top K.
+        // A warp takes batches of 32 hits: one lane loads each hit's frontier
+        // entries, then groups of G lanes score H = 32 / G hits at a time over
+        // G rounds, so every warp keeps H hits' embedding rows in flight.
         const uint16_t* relsrc = sm.dir ? g.rel : g.rrel;
         const ListEnt* nearL = P->list + sm.near_base;
         const float* w1s = P->w32 + sm.a_base;
         const float* w3s = P->w32 + sm.c_base;
-        int h = warp;
-        uint32_t slice = 0;
-        bool have_w2 = false;
-        float w2 = 0.f;
+        const int G = P->score_width, H = 32 / G;
+        const int sub = lane & (G - 1);
+        int b = warp;              // current batch of 32 hits
+        bool loaded = false;
+        unsigned pend = 0;         // lanes whose hit still has combinations to expand
+        uint32_t slice = 0;        // this lane's next combination
+        uint32_t hu = 0, hv = 0, hr2 = 0, has = 0, hal = 0, hcs = 0, hcl = 0;
+        float hw2 = 0.f;
         for (;;) {
             const int budget = (kCandCap - sm.round_cnt) / kMidWarps;
             int used = 0;
             bool done = true;
             if (!sm.local_dense) {
                 const float thr = sm.thr_keep;
-                while (h < nh) {
-                    const Hit ht = hits[h];
-                    const ListEnt ne = nearL[ht.near_k];
-                    const ListEnt fe = far[ht.far_k];
-                    const ListEnt& ea = sm.dir ? ne : fe;  // hop-1 side (u)
-                    const ListEnt& ec = sm.dir ? fe : ne;  // hop-3 side (v)
-                    if (!have_w2) {
-                        const uint32_t r2 = relsrc[ht.epos];
-                        w2 = edge_w32_group(g, ea.vertex, r2, ec.vertex, lane, 32);
-                        have_w2 = true;
-                        slice = 0;
-                        const float smax = __fadd_rn(__fadd_rn(ea.maxw, w2), ec.maxw);
-                        if (smax < thr) {
-                            if (lane == 0) n_paths_w += ea.run_len * ec.run_len;
-                            h += kMidWarps;
-                            have_w2 = false;
-                            continue;
+                for (;;) {
+                    if (!loaded) {
+                        const int hb = b * 32;
+                        if (hb >= nh) break;
+                        const int hi = hb + lane;
+                        const bool live = hi < nh;
+                        float mw1 = 0.f, mw3 = 0.f;
+                        hu = hv = hr2 = 0;
+                        has = hal = hcs = hcl = 0;
+                        if (live) {
+                            const Hit ht = hits[hi];
+                            const ListEnt ne = nearL[ht.near_k];
+                            const ListEnt fe = far[ht.far_k];
+                            const ListEnt& ea = sm.dir ? ne : fe;  // hop-1 side (u)
+                            const ListEnt& ec = sm.dir ? fe : ne;  // hop-3 side (v)
+                            hu = ea.vertex;
+                            hv = ec.vertex;
+                            hr2 = relsrc[ht.epos];
+                            has = ea.run_start;
+                            hal = ea.run_len;
+                            hcs = ec.run_start;
+                            hcl = ec.run_len;
+                            mw1 = ea.maxw;
+                            mw3 = ec.maxw;
+                            n_paths_w += static_cast<unsigned long long>(hal) * hcl;
                         }
+                        float w2m = 0.f;
+#pragma unroll 2
+                        for (int r = 0; r < G; ++r) {
+                            const int src = r * H + lane / G;
+                            const uint32_t u = __shfl_sync(FULL, hu, src);
+                            const uint32_t v = __shfl_sync(FULL, hv, src);
+                            const uint32_t rr = __shfl_sync(FULL, hr2, src);
+                            const float w = edge_w32_group(g, u, rr, v, sub, G);
+                            const float tw = __shfl_sync(FULL, w, ((lane - r * H) & (H - 1)) * G);
+                            if (lane / H == r) w2m = tw;
+                        }
+                        hw2 = w2m;
+                        const float smax = __fadd_rn(__fadd_rn(mw1, hw2), mw3);
+                        pend = __ballot_sync(FULL, live && smax >= thr);
+                        loaded = true;
+                        slice = 0;
                     }
-                    const uint32_t na = ea.run_len, nc = ec.run_len;
-                    const uint32_t total = na * nc;
-                    if (slice == 0 && lane == 0) n_paths_w += total;
+                    // each lane walks the (r1, r3) combinations of its own hit
                     bool stop = false;
-                    while (slice < total) {
-                        const uint32_t c = slice + lane;
+                    for (;;) {
+                        const bool act = (pend >> lane) & 1u;
+                        if (!__any_sync(FULL, act)) break;
                         bool keep = false;
                         Cand cd;
-                        if (c < total) {
-                            const uint32_t i = c / nc, j = c - i * nc;
-                            const float w1 = w1s[ea.run_start + i];
-                            const float w3 = w3s[ec.run_start + j];
-                            const float s32 = __fadd_rn(__fadd_rn(w1, w2), w3);
+                        if (act) {
+                            uint32_t i = slice, j = 0;
+                            if (hcl != 1) {
+                                i = slice / hcl;
+                                j = slice - i * hcl;
+                            }
+                            const float s32 = __fadd_rn(__fadd_rn(w1s[has + i], hw2), w3s[hcs + j]);
                             keep = s32 >= thr;
                             cd.s32 = s32;
-                            cd.a_idx = ea.run_start + i;
-                            cd.c_idx = ec.run_start + j;
-                            cd.r2 = relsrc[ht.epos];
+                            cd.a_idx = has + i;
+                            cd.c_idx = hcs + j;
+                            cd.r2 = static_cast<uint16_t>(hr2);
                             cd.pad = 0;
                         }
-                        const unsigned b = __ballot_sync(FULL, keep);
-                        const int nk2 = __popc(b);
+                        const unsigned bal = __ballot_sync(FULL, keep);
+                        const int nk2 = __popc(bal);
                         if (used + nk2 > budget) {
                             stop = true;
                             break;
                         }
                         if (nk2) {
                             int base = 0;
-                            const int leader = __ffs(b) - 1;
+                            const int leader = __ffs(bal) - 1;
                             if (lane == leader) base = atomicAdd(&sm.cand_cnt, nk2);
                             base = __shfl_sync(FULL, base, leader);
-                            if (keep) sm.cand[base + __popc(b & lanemask_lt())] = cd;
+                            if (keep) sm.cand[base + __popc(bal & lanemask_lt())] = cd;
                         }
                         used += nk2;
-                        slice += 32;
+                        if (act) {
+                            ++slice;
+                            if (slice >= hal * hcl) pend &= ~(1u << lane);
+                        }
+                        pend = __ballot_sync(FULL, (pend >> lane) & 1u);
                     }
                     if (stop) {
                         done = false;
                         break;
                     }
-                    h += kMidWarps;
-                    have_w2 = false;
+                    loaded = false;
+                    b += kMidWarps;
                 }
             }
             if (!__syncthreads_or(done ? 0 : 1)) break;
             flush_cands(sm, P, K, two_err);
         }
         __syncthreads();
+        if (!sm.local_dense && (sm.lt_key == 0u ? sm.cand_cnt >= K : sm.cand_cnt > kCandCap / 2))
+            flush_cands(sm, P, K, two_err);
+        MHR_PHASE(3);
     }
     if (cur_q >= 0) finish_query(sm, P, K, two_err, &n_cands);
+    MHR_PHASE(0);
+#ifdef MHR_PHASE_TIMING
+    if (threadIdx.x == 0) printf("MHR_PHASE %d %llu %llu %llu %llu\n", blockIdx.x, ph[0], ph[1], ph[2], ph[3]);
+#endif
     if (threadIdx.x == 0) {
         atomicAdd(&P->counters[kCntScanned], n_scanned);
         atomicAdd(&P->counters[kCntHits], n_hits);
         atomicAdd(&P->counters[kCntCands], n_cands);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n_paths_w += __shfl_xor_sync(FULL, n_paths_w, o);
     if (lane == 0 && n_paths_w) atomicAdd(&P->counters[kCntPaths], n_paths_w);
 }
 
@@ -805,13 +908,37 @@ __global__ void __launch_bounds__(1024) k_merge1(const PlanDev* __restrict__ P) 
     }
 }
 
-__global__ void k_rescore(const PlanDev* __restrict__ P, DevGraph g) {
+// fp64 rescoring of the band, one warp per candidate.  The canonical order
+// fixes only the accumulation acc = acc + y_j (j ascending); the terms
+// y_j = |(a_j + b_j) - c_j| (or (a_j * b_j) * c_j) are independent, so lanes
+// compute them in parallel into shared memory and three lanes (one per edge)
+// then run the three sequential fp64 sums.
+constexpr int kRsWarps = 8;
+constexpr int kRsChunk = 256;
+
+__device__ __forceinline__ double term64(const DevGraph& g, uint32_t h, uint32_t r, uint32_t t, int j) {
+    const double a = emb_f64(g.vemb, g.dtype, h, g.d, j);
+    const double b = emb_f64(g.remb, g.dtype, r, g.d, j);
+    const double c = emb_f64(g.vemb, g.dtype, t, g.d, j);
+    if (g.fn == MHR_SCORE_TRANSE_L1) return fabs(__dsub_rn(__dadd_rn(a, b), c));
+    return __dmul_rn(__dmul_rn(a, b), c);
+}
+
+__global__ void __launch_bounds__(kRsWarps * 32) k_rescore(const PlanDev* __restrict__ P, DevGraph g) {
+    __shared__ double ys[kRsWarps][3][kRsChunk];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t total = static_cast<int64_t>(P->nq) * P->band_cap;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total; x += stride) {
+    const int64_t gw = blockIdx.x * static_cast<int64_t>(kRsWarps) + w;
+    const int64_t nw = static_cast<int64_t>(gridDim.x) * kRsWarps;
+    for (int64_t x = gw; x < total; x += nw) {
         const int q = static_cast<int>(x / P->band_cap);
         const int i = static_cast<int>(x - static_cast<int64_t>(q) * P->band_cap);
-        if (i >= P->band_cnt[q] || P->dense[q]) continue;
+        if (i >= P->band_cnt[q] || P->dense[q]) {
+            // skip the rest of this query's empty band slots
+            const int64_t next = static_cast<int64_t>(q + 1) * P->band_cap;
+            if (next > x + nw) x += ((next - x - 1) / nw) * nw;
+            continue;
+        }
         const Cand c = P->band_cand[x];
         const uint32_t s = P->S[q], t = P->T[q];
         const int64_t p1 = g.off[s] + c.a_idx;
@@ -823,11 +950,25 @@ __global__ void k_rescore(const PlanDev* __restrict__ P, DevGraph g) {
         p.r3 = g.rrel[p3];
         p.r2 = c.r2;
         p.pad = 0;
-        const double w1 = edge_w64(g, s, p.r1, p.u);
-        const double w2 = edge_w64(g, p.u, p.r2, p.v);
-        const double w3 = edge_w64(g, p.v, p.r3, t);
-        p.score = __dadd_rn(__dadd_rn(w1, w2), w3);
-        P->band_path[x] = p;
+        const uint32_t hh[3] = {s, p.u, p.v}, rr[3] = {p.r1, p.r2, p.r3}, tt[3] = {p.u, p.v, t};
+        double acc = 0.0;
+        for (int c0 = 0; c0 < g.d; c0 += kRsChunk) {
+            const int n = min(kRsChunk, g.d - c0);
+            for (int j = lane; j < n; j += 32) {
+#pragma unroll
+                for (int e = 0; e < 3; ++e) ys[w][e][j] = term64(g, hh[e], rr[e], tt[e], c0 + j);
+            }
+            __syncwarp();
+            if (lane < 3)
+                for (int j = 0; j < n; ++j) acc = __dadd_rn(acc, ys[w][lane][j]);
+            __syncwarp();
+        }
+        double we = (g.fn == MHR_SCORE_TRANSE_L1) ? __dsub_rn(g.gamma, acc) : acc;
+        const double w1 = __shfl_sync(FULL, we, 0), w2 = __shfl_sync(FULL, we, 1), w3 = __shfl_sync(FULL, we, 2);
+        if (lane == 0) {
+            p.score = __dadd_rn(__dadd_rn(w1, w2), w3);
+            P->band_path[x] = p;
+        }
     }
 }
 
@@ -1157,7 +1298,7 @@ static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int
         k_middle<kUnroll><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
     } else {
         k_merge1<<<std::min(p->nq, sms * 2), 1024, 0, st>>>(d);
-        k_rescore<<<sms * 4, 128, 0, st>>>(d, g);
+        k_rescore<<<sms * 4, kRsWarps * 32, 0, st>>>(d, g);
         k_merge2<<<std::min(p->nq, sms * 2), 1024, merge2_smem_bytes(p->h.band_cap), st>>>(d);
         k_exact<<<std::min(p->nq, sms * 2), 1024, exact_smem_bytes(), st>>>(d, g);
     }
@@ -1195,6 +1336,15 @@ static cudaError_t launch_graphs(Plan* p, cudaStream_t st) {
     return cudaEventRecord(p->ev[3], st);
 }
 
+// lanes that score one edge together: about two 16-byte vectors per lane per row
+static int hit_group_width(int d, int dtype) {
+    const int vec = (dtype == MHR_F32) ? ((d & 3) == 0 ? d / 4 : d) : ((d & 7) == 0 ? d / 8 : d);
+    const int want = (vec + 1) / 2;
+    int w = 1;
+    while (w < want && w < 32) w <<= 1;
+    return w;
+}
+
 static int choose_sigma(int64_t n) {
     int sigma = 0;
     while (((n - 1) >> sigma) >= static_cast<int64_t>(kMaxBmWords) * 32) ++sigma;
@@ -1216,6 +1366,7 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) 
     h.pq = 8 * K + 2048;
     h.band_cap = K + 2048;
     h.err_path = G->err_path;
+    h.score_width = hit_group_width(G->dg.d, G->dg.dtype);
     mhr_status rc = MHR_OK;
     auto bail = [&](mhr_status r) {
         delete p;
@@ -1239,6 +1390,8 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) 
     if ((rc = plan_alloc(p, &h.n_out, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.counters, kCntCount)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.partials, kScanGrid + 1)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.cursors, p->grid)) != MHR_OK) return bail(rc);
+    h.grid = p->grid;
     const RegionLayout L = region_layout(nq);
     p->region_bytes = L.total;
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p->dregion), L.total);

@@ -64,7 +64,8 @@ enum {
 // a captured CUDA graph keeps working when buffers are regrown between calls.
 struct PlanDev {
     int32_t nq, K, chunk, sigma;
-    int32_t nbw, pq, band_cap, pad0;
+    int32_t nbw, pq, band_cap, score_width;
+    int32_t grid, pad1;  // persistent CTAs of the join
     int64_t X;     // slots = totA + totC
     int64_t totA;  // slots of the hop-1 side
     double err_path;
@@ -100,6 +101,7 @@ struct PlanDev {
     mhr_path* out;      // [nq x K]
     int32_t* n_out;     // [nq]
     unsigned long long* counters;  // kCntCount
+    unsigned long long* cursors;   // [grid] next item of each CTA's own range
     int64_t* partials;             // scan scratch
 };
 

@@ -292,3 +292,26 @@ def test_medium_workload_sampled(mhr):
     want, n_want = oracle.topk_paths_batch(g, S[sample], T[sample], K)
     for i, q in enumerate(sample):
         compare_query(out[q], int(n_out[q]), want[i, : n_want[i]], ctx=int(q))
+
+
+def test_work_counters_match_oracle(mhr):
+    """edges_scanned = sum min(S_f, S_b); hits = middle edges joining the two
+    frontiers; paths = all simple three-hop paths (counted by the oracle)."""
+    g = synth.gen_rmat_kg(13, 6000, 120_000, 5, 3, seed=14)
+    g.vemb, g.remb = synth.gen_embeddings(g.n, g.R, 16, 0.25, seed=14)
+    S, T = synth.queries_edge_biased(g, 24, seed=14)
+    G = mhr.load_kg(g)
+    for chunk in (64, 16384):
+        out, n_out, st = mhr.mhr_topk_paths_batched(G, S, T, 50, opts={"chunk": chunk}, with_stats=True)
+        scanned = hits = paths = 0
+        for s, t in zip(S.tolist(), T.tolist()):
+            qs = oracle.query_stats(g, s, t)
+            _, h, p = oracle.topk_paths(g, s, t, 1, with_counts=True)
+            scanned += min(qs["s_f"], qs["s_b"])
+            hits += h
+            paths += p
+        assert st["edges_scanned"] == scanned
+        assert st["hits"] == hits
+        assert st["paths"] == paths
+        assert st["ms_join"] > 0 and st["ms_device"] >= st["ms_join"]
+    G.close()
