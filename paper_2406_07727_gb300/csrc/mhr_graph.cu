@@ -272,6 +272,44 @@ __global__ void k_edge_scores64(DevGraph g, const uint32_t* __restrict__ src,
     }
 }
 
+// per-vertex maximum fp32 weight over out-edges and in-edges (order keys)
+__global__ void k_vertex_maxw(DevGraph g, int width, uint32_t* __restrict__ kout, uint32_t* __restrict__ kin) {
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (width - 1);
+    const int64_t group = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / width;
+    const int64_t ngroups = (static_cast<int64_t>(gridDim.x) * blockDim.x) / width;
+    const int64_t iters = (g.E + ngroups - 1) / ngroups;
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t i = group + it * ngroups;
+        const bool live = i < g.E;
+        uint32_t u = 0, r = 0, v = 0;
+        if (live) {
+            u = static_cast<uint32_t>(row_of_edge(g.off, g.n, i));
+            r = g.rel[i];
+            v = g.col[i];
+        }
+        const float w = edge_w32_group(g, u, r, v, sub, width);
+        if (live && sub == 0) {
+            const uint32_t k = f2key(w);
+            atomicMax(&kout[u], k);
+            atomicMax(&kin[v], k);
+        }
+    }
+}
+
+// keys -> fp32 upper bounds: + slack (two fp32 evaluations of one edge in
+// different summation orders differ by at most 2 * eps32), rounded up
+__global__ void k_maxw_finish(uint32_t* __restrict__ a, int64_t n, double slack) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+        const uint32_t k = a[i];
+        float f;
+        if (k == 0u) f = __int_as_float(0xff800000);
+        else f = __double2float_ru(__dadd_ru(static_cast<double>(key2f(k)), slack));
+        a[i] = __float_as_uint(f);
+    }
+}
+
 }  // namespace mhr
 
 using namespace mhr;
@@ -440,6 +478,21 @@ mhr_status load_impl(const mhr_graph_desc* desc, mhr_graph* g, cudaStream_t st) 
     dg.remb = remb;
     g->fn = desc->score_fn;
     compute_bounds(g);
+    // per-vertex bounds on the fp32 weight of adjacent edges (bound pruning)
+    {
+        uint32_t *kout, *kin;
+        MHR_TRY(graph_alloc(g, reinterpret_cast<void**>(&kout), sizeof(uint32_t) * n));
+        MHR_TRY(graph_alloc(g, reinterpret_cast<void**>(&kin), sizeof(uint32_t) * n));
+        MHR_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(uint32_t) * n, st));
+        MHR_CUDA_TRY(cudaMemsetAsync(kin, 0, sizeof(uint32_t) * n, st));
+        if (E) k_vertex_maxw<<<grid, 256, 0, st>>>(dg, score_group_width(d, desc->emb_dtype), kout, kin);
+        k_maxw_finish<<<grid, 256, 0, st>>>(kout, n, 2.0 * g->eps32_edge);
+        k_maxw_finish<<<grid, 256, 0, st>>>(kin, n, 2.0 * g->eps32_edge);
+        MHR_CUDA_TRY(cudaGetLastError());
+        MHR_CUDA_TRY(cudaStreamSynchronize(st));
+        dg.maxw_out = reinterpret_cast<const float*>(kout);
+        dg.maxw_in = reinterpret_cast<const float*>(kin);
+    }
     const double big = 1e30;
     if (!(g->max_l1 < big && g->max_rel_l1 < big && g->max_l2sq < big && g->max_rel_inf < big &&
           g->err_path < 1e20))

@@ -49,6 +49,10 @@ struct DevGraph {
     const uint8_t* vtypes;
     const void* vemb;      // [n x d] f32 or bf16
     const void* remb;      // [R x d]
+    // upper bounds (fp32, rounded up, any summation order) of the fp32 edge
+    // weight over the out-edges / in-edges of each vertex; -inf if none
+    const float* maxw_out;
+    const float* maxw_in;
 };
 
 // device allocation owned by the graph

@@ -170,6 +170,8 @@ __global__ void k_init(const PlanDev* __restrict__ P, DevGraph g) {
         const uint32_t s = P->S[q], t = P->T[q];
         P->status[q] = (s < g.n && t < g.n && s != t) ? 0 : 1;
         P->thr_g[q] = 0u;
+        P->qmax[2 * q] = 0u;
+        P->qmax[2 * q + 1] = 0u;
         P->dense[q] = 0;
         P->pool_cnt[q] = 0;
         P->band_cnt[q] = 0;
@@ -270,6 +272,7 @@ __global__ void k_lists(const PlanDev* __restrict__ P, DevGraph g) {
         }
         P->list[base + j] = e;
         P->degv[base + j] = e.deg;
+        atomicMax(&P->qmax[2 * q + (sideA ? 0 : 1)], f2key(mw));
     }
 }
 
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(1024) k_plan(const PlanDev* __restrict__ P) {
 }
 
 // near-side entries: (prefix of scan degree, row start)
-__global__ void k_near(const PlanDev* __restrict__ P) {
+__global__ void k_near(const PlanDev* __restrict__ P, DevGraph g) {
     const int64_t X = P->X, totA = P->totA;
     const int nq = P->nq;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -320,13 +323,23 @@ __global__ void k_near(const PlanDev* __restrict__ P) {
         if ((P->dir[q] == 1) != sideA) continue;
         const int64_t base = sideA ? offs[q] : totA + offs[q];
         if (x - base >= P->near_cnt[q]) continue;
-        P->nearP[x] = make_uint2(static_cast<uint32_t>(P->scan2[x] - P->scan2[base]), P->list[x].rowstart);
+        const ListEnt e = P->list[x];
+        P->nearP[x] = make_uint2(static_cast<uint32_t>(P->scan2[x] - P->scan2[base]), e.rowstart);
+        // any path through this near entry scores (in fp32) at most:
+        //   forward  (near = u): maxw1(u) + maxw_out(u) + max_v maxw3(v)
+        //   backward (near = v): max_u maxw1(u) + maxw_in(v) + maxw3(v)
+        float b;
+        if (sideA) b = __fadd_rn(__fadd_rn(e.maxw, g.maxw_out[e.vertex]), key2f(P->qmax[2 * q + 1]));
+        else b = __fadd_rn(__fadd_rn(key2f(P->qmax[2 * q]), g.maxw_in[e.vertex]), e.maxw);
+        P->nearB[x] = b;
     }
 }
 
 // ===========================================================================
 // the middle join (persistent)
 // ===========================================================================
+constexpr int kRelCacheVecs = 512;  // 8 KB of fp32 relation embeddings
+
 struct MidSmem {
     uint32_t bm[kMaxBmWords];
     uint32_t rank[kMaxRank + 8];
@@ -336,6 +349,8 @@ struct MidSmem {
     uint32_t bc[4];
     int64_t red[33];
     uint32_t redu[33];
+    float4 relc[kRelCacheVecs];  // relation embeddings (fp32) when R*d fits
+    uint8_t compact[kMidWarps][32];  // per-warp lane map of surviving hits
     // per-query state
     int q, dir, near_cnt, far_cnt, local_dense, skip;
     uint32_t s, t;
@@ -475,6 +490,57 @@ __device__ void setup_query(MidSmem& sm, const PlanDev* __restrict__ P, int q) {
     __syncthreads();
 }
 
+__device__ __forceinline__ float4 ld4(const float* base, int64_t row, int d, int j) {
+    return __ldg(reinterpret_cast<const float4*>(base + row * d) + j);
+}
+
+__device__ __forceinline__ float term4(const float4& h, const float4& r, const float4& t, bool transe) {
+    if (transe)
+        return fabsf(__fsub_rn(__fadd_rn(h.x, r.x), t.x)) + fabsf(__fsub_rn(__fadd_rn(h.y, r.y), t.y)) +
+               fabsf(__fsub_rn(__fadd_rn(h.z, r.z), t.z)) + fabsf(__fsub_rn(__fadd_rn(h.w, r.w), t.w));
+    return (h.x * r.x) * t.x + (h.y * r.y) * t.y + (h.z * r.z) * t.z + (h.w * r.w) * t.w;
+}
+
+// fp32 weight of the middle edge (u, r, v) for the f32 rows with d = 4*vec,
+// vec <= 2G: lane `sub` of a group of G owns vectors sub and sub + G.  The
+// near-side row (the scanned vertex) stays in registers across the group's
+// consecutive hits, the relation row comes from shared memory when cached,
+// and only the far-side row is fetched per hit.
+struct NearRow {
+    float4 a, b;
+    uint32_t id;
+};
+
+__device__ __forceinline__ float hit_w32_f32(const DevGraph& g, NearRow& nr, uint32_t near_v, uint32_t far_v,
+                                             uint32_t r, bool fwd, int sub, int G, int vec,
+                                             const float4* relc) {
+    const float* E = static_cast<const float*>(g.vemb);
+    const float* Rw = static_cast<const float*>(g.remb);
+    const bool has0 = sub < vec, has1 = sub + G < vec;
+    if (near_v != nr.id) {
+        nr.a = has0 ? ld4(E, near_v, g.d, sub) : make_float4(0.f, 0.f, 0.f, 0.f);
+        nr.b = has1 ? ld4(E, near_v, g.d, sub + G) : make_float4(0.f, 0.f, 0.f, 0.f);
+        nr.id = near_v;
+    }
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 f0 = has0 ? ld4(E, far_v, g.d, sub) : z;
+    const float4 f1 = has1 ? ld4(E, far_v, g.d, sub + G) : z;
+    float4 r0, r1;
+    if (relc) {
+        r0 = has0 ? relc[r * vec + sub] : z;
+        r1 = has1 ? relc[r * vec + sub + G] : z;
+    } else {
+        r0 = has0 ? ld4(Rw, r, g.d, sub) : z;
+        r1 = has1 ? ld4(Rw, r, g.d, sub + G) : z;
+    }
+    const bool transe = g.fn == MHR_SCORE_TRANSE_L1;
+    float acc;
+    if (fwd) acc = (has0 ? term4(nr.a, r0, f0, transe) : 0.f) + (has1 ? term4(nr.b, r1, f1, transe) : 0.f);
+    else acc = (has0 ? term4(f0, r0, nr.a, transe) : 0.f) + (has1 ? term4(f1, r1, nr.b, transe) : 0.f);
+    for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+    return transe ? __fsub_rn(g.gamma32, acc) : acc;
+}
+
 template <int UNROLL>
 __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __restrict__ P, DevGraph g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -486,7 +552,8 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
     const double two_err = 2.0 * P->err_path;
     const int64_t total_items = P->item_off[nq];
     Hit* hits = P->hits + static_cast<int64_t>(blockIdx.x) * kMaxChunk;
-    unsigned long long n_scanned = 0, n_hits = 0, n_cands = 0, n_paths_w = 0;
+    unsigned long long n_scanned = 0, n_hits = 0, n_cands = 0, n_paths_w = 0, n_pruned = 0;
+    const bool prune = P->prune != 0;
 #ifdef MHR_PHASE_TIMING
     // cycles per phase, thread 0: 0 fetch + query switch, 1 item setup, 2 scan, 3 score
     unsigned long long ph[4] = {0, 0, 0, 0};
@@ -507,6 +574,14 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
     int cur_q = -1;
     int victim = 0;  // thread 0: offset of the range it currently drains
     if (threadIdx.x == 0) sm.q = -1;
+    // fast hit scorer: fp32 rows of at most 2G vectors per lane group
+    const int vec4 = g.d / 4;
+    const bool fast = g.dtype == MHR_F32 && (g.d & 3) == 0 && vec4 <= 2 * P->score_width;
+    const bool relc_ok = fast && g.R * vec4 <= kRelCacheVecs;
+    if (relc_ok)
+        for (int i = threadIdx.x; i < g.R * vec4; i += blockDim.x)
+            sm.relc[i] = reinterpret_cast<const float4*>(g.remb)[i];
+    // (the first __syncthreads of the item loop publishes the cache)
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -624,18 +699,25 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         const uint32_t* colsrc = sm.dir ? g.col : g.rcol;
         const ListEnt* far = P->list + sm.far_base;
         const int far_cnt = sm.far_cnt;
+        const float* nearB = P->nearB + sm.near_base;
+        const float thr_scan = sm.thr_keep;
         for (int gb = warp * UNROLL; gb < ngroups; gb += kMidWarps * UNROLL) {
             uint2 ne[UNROLL];
             uint32_t kk[UNROLL];
+            float rb[UNROLL];
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
                 const int gidx = gb + u;
                 ne[u] = make_uint2(s_near32, 0u);
                 kk[u] = 0;
+                rb[u] = 0.f;
                 if (gidx < ngroups) {
                     kk[u] = sm.gmap[gidx] - 1u;
                     const uint32_t idx = kk[u] + lane;
-                    if (idx < static_cast<uint32_t>(near_cnt)) ne[u] = nearP[idx];
+                    if (idx < static_cast<uint32_t>(near_cnt)) {
+                        ne[u] = nearP[idx];
+                        if (prune) rb[u] = nearB[idx];
+                    }
                 }
             }
             uint32_t xv[UNROLL], epos[UNROLL], nk[UNROLL];
@@ -657,6 +739,14 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                     const uint32_t pm = __shfl_sync(FULL, ne[u].x, c);
                     const uint32_t rs = __shfl_sync(FULL, ne[u].y, c);
                     valid[u] = e < e1;
+                    if (prune) {
+                        // no path through this row can reach the kept band: skip its edges
+                        const float rowb = __shfl_sync(FULL, rb[u], c);
+                        if (valid[u] && rowb < thr_scan) {
+                            valid[u] = false;
+                            ++n_pruned;
+                        }
+                    }
                     epos[u] = rs + (e - pm);
                     nk[u] = kk[u] + c;
                 }
@@ -736,6 +826,8 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         uint32_t slice = 0;        // this lane's next combination
         uint32_t hu = 0, hv = 0, hr2 = 0, has = 0, hal = 0, hcs = 0, hcl = 0;
         float hw2 = 0.f;
+        NearRow nrow;
+        nrow.id = 0xffffffffu;
         for (;;) {
             const int budget = (kCandCap - sm.round_cnt) / kMidWarps;
             int used = 0;
@@ -751,6 +843,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                         float mw1 = 0.f, mw3 = 0.f;
                         hu = hv = hr2 = 0;
                         has = hal = hcs = hcl = 0;
+                        bool alive = false;
                         if (live) {
                             const Hit ht = hits[hi];
                             const ListEnt ne = nearL[ht.near_k];
@@ -767,21 +860,56 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                             mw1 = ea.maxw;
                             mw3 = ec.maxw;
                             n_paths_w += static_cast<unsigned long long>(hal) * hcl;
+                            alive = true;
+                            if (prune) {
+                                // w2 <= max weight of the scanned vertex's adjacent edges
+                                const float mw2 = sm.dir ? g.maxw_out[hu] : g.maxw_in[hv];
+                                if (__fadd_rn(__fadd_rn(mw1, mw2), mw3) < thr) {
+                                    alive = false;
+                                    ++n_pruned;
+                                }
+                            }
                         }
+                        // move the surviving hits to the low lanes
+                        const unsigned am = __ballot_sync(FULL, alive);
+                        const int nsurv = __popc(am);
+                        if (prune) {
+                            if (alive) sm.compact[warp][__popc(am & lanemask_lt())] = static_cast<uint8_t>(lane);
+                            __syncwarp();
+                            const int src = lane < nsurv ? sm.compact[warp][lane] : lane;
+                            __syncwarp();
+                            hu = __shfl_sync(FULL, hu, src);
+                            hv = __shfl_sync(FULL, hv, src);
+                            hr2 = __shfl_sync(FULL, hr2, src);
+                            has = __shfl_sync(FULL, has, src);
+                            hal = __shfl_sync(FULL, hal, src);
+                            hcs = __shfl_sync(FULL, hcs, src);
+                            hcl = __shfl_sync(FULL, hcl, src);
+                            mw1 = __shfl_sync(FULL, mw1, src);
+                            mw3 = __shfl_sync(FULL, mw3, src);
+                        }
+                        const bool live2 = prune ? (lane < nsurv) : live;
+                        const int rounds = prune ? (nsurv + H - 1) / H : G;
                         float w2m = 0.f;
-#pragma unroll 2
-                        for (int r = 0; r < G; ++r) {
+                        for (int r = 0; r < rounds; ++r) {
                             const int src = r * H + lane / G;
                             const uint32_t u = __shfl_sync(FULL, hu, src);
                             const uint32_t v = __shfl_sync(FULL, hv, src);
                             const uint32_t rr = __shfl_sync(FULL, hr2, src);
-                            const float w = edge_w32_group(g, u, rr, v, sub, G);
+                            float w;
+                            if (fast) {
+                                const bool fwd = sm.dir != 0;
+                                w = hit_w32_f32(g, nrow, fwd ? u : v, fwd ? v : u, rr, fwd, sub, G, vec4,
+                                                relc_ok ? sm.relc : nullptr);
+                            } else {
+                                w = edge_w32_group(g, u, rr, v, sub, G);
+                            }
                             const float tw = __shfl_sync(FULL, w, ((lane - r * H) & (H - 1)) * G);
                             if (lane / H == r) w2m = tw;
                         }
                         hw2 = w2m;
                         const float smax = __fadd_rn(__fadd_rn(mw1, hw2), mw3);
-                        pend = __ballot_sync(FULL, live && smax >= thr);
+                        pend = __ballot_sync(FULL, live2 && smax >= thr);
                         loaded = true;
                         slice = 0;
                     }
@@ -852,6 +980,9 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         atomicAdd(&P->counters[kCntHits], n_hits);
         atomicAdd(&P->counters[kCntCands], n_cands);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n_pruned += __shfl_xor_sync(FULL, n_pruned, o);
+    if (lane == 0 && n_pruned) atomicAdd(&P->counters[kCntPruned], n_pruned);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) n_paths_w += __shfl_xor_sync(FULL, n_paths_w, o);
     if (lane == 0 && n_paths_w) atomicAdd(&P->counters[kCntPaths], n_paths_w);
@@ -1244,7 +1375,7 @@ static size_t merge2_smem_bytes(int band_cap) {
 static mhr_status ensure_slots(Plan* p, int64_t X) {
     if (X <= p->slot_cap && p->slot_mem) return MHR_OK;
     int64_t cap = std::max<int64_t>(X, std::max<int64_t>(p->slot_cap * 2, 1 << 16));
-    // per slot: w32 4, flag 4, degv 4, scan1 8, scan2 8, list 24, nearP 8
+    // per slot: w32 4, flag 4, degv 4, scan1 8, scan2 8, list 24, nearP 8, nearB 4
     const size_t a8 = 256;
     size_t o = 0;
     const size_t o_w32 = o; o = align_up(o + 4 * cap, a8);
@@ -1254,6 +1385,7 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
     const size_t o_s2 = o; o = align_up(o + 8 * (cap + 1), a8);
     const size_t o_list = o; o = align_up(o + sizeof(ListEnt) * cap, a8);
     const size_t o_near = o; o = align_up(o + sizeof(uint2) * cap, a8);
+    const size_t o_nb = o; o = align_up(o + sizeof(float) * cap, a8);
     void* mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, o);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (frontier slots)");
@@ -1271,6 +1403,7 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
     p->h.scan2 = reinterpret_cast<int64_t*>(b + o_s2);
     p->h.list = reinterpret_cast<ListEnt*>(b + o_list);
     p->h.nearP = reinterpret_cast<uint2*>(b + o_near);
+    p->h.nearB = reinterpret_cast<float*>(b + o_nb);
     // scan kernels take raw pointers, so a new buffer needs a new capture
     p->drop_graphs();
     return MHR_OK;
@@ -1293,7 +1426,7 @@ static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int
         e = device_excl_scan<uint32_t>(p->h.degv, nX, p->h.partials, p->h.scan2, st);
         if (e != cudaSuccess) return e;
         k_plan<<<1, 1024, 0, st>>>(d);
-        k_near<<<sms * 4, 256, 0, st>>>(d);
+        k_near<<<sms * 4, 256, 0, st>>>(d, g);
     } else if (part == 1) {
         k_middle<kUnroll><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
     } else {
@@ -1379,6 +1512,7 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) 
     if ((rc = plan_alloc(p, &h.s_near, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.item_off, nq + 1)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.thr_g, nq)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.qmax, 2 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.dense, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.pool_cnt, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.band_cnt, nq)) != MHR_OK) return bail(rc);
@@ -1478,6 +1612,7 @@ static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint
     MHR_TRY(ensure_slots(p, ta + tc));
     p->h.X = ta + tc;
     p->h.totA = ta;
+    p->h.prune = (opts && opts->prune) ? 1 : 0;
     std::memcpy(p->pin, &p->h, sizeof(PlanDev));
     MHR_CUDA_TRY(cudaMemcpyAsync(p->dregion, p->pin, L.total, cudaMemcpyHostToDevice, st));
     MHR_CUDA_TRY(cudaEventRecord(p->h2d_done, st));

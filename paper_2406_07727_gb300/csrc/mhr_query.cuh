@@ -65,7 +65,7 @@ enum {
 struct PlanDev {
     int32_t nq, K, chunk, sigma;
     int32_t nbw, pq, band_cap, score_width;
-    int32_t grid, pad1;  // persistent CTAs of the join
+    int32_t grid, prune;  // persistent CTAs of the join; bound pruning on/off
     int64_t X;     // slots = totA + totC
     int64_t totA;  // slots of the hop-1 side
     double err_path;
@@ -82,6 +82,7 @@ struct PlanDev {
     uint32_t* degv;
     int64_t* scan2;
     uint2* nearP;  // (prefix of scan degree within the query, row start)
+    float* nearB;  // upper bound of the fp32 score of any path through a near entry
     // per query [nq] (+1 for item_off)
     int32_t* status;
     int32_t* dir;       // 1 = forward (scan out-rows of hop-1 vertices), 0 = backward
@@ -90,6 +91,7 @@ struct PlanDev {
     int64_t* s_near;
     int64_t* item_off;
     uint32_t* thr_g;    // order-preserving key of the best known K-th fp32 score
+    uint32_t* qmax;     // [2 nq] keys: max hop-1 weight, max hop-3 weight
     int32_t* dense;
     int32_t* pool_cnt;
     int32_t* band_cnt;
