@@ -168,6 +168,32 @@ mhr_status mhr_topk_paths_batched(const mhr_graph* g, int32_t nq, const uint32_t
                                   mhr_mem mem, const mhr_query_opts* opts, mhr_stats* stats,
                                   void* cuda_stream);
 
+/*
+ * mhr_topk_paths_noalloc - one query, like mhr_topk_paths, for callers that
+ * cannot allocate device memory.  The paper has no counterpart; this is a
+ * deployment entry point.  Callers that cannot allocate: services that must
+ * keep a fixed device-memory footprint once started, hosts whose own
+ * allocator owns the device memory (a raw allocation would fail or fragment
+ * it), and latency-critical sections where the implicit device
+ * synchronisation of cudaMalloc/cudaFree is not acceptable.
+ *   out    device array of K mhr_path; n_out device pointer to one int32
+ *          (paths written).  Same result as mhr_topk_paths (same order,
+ *          bit-identical scores).
+ *   Asynchronous on cuda_stream.  Allocates nothing: its only scratch is a
+ *   fixed device array of about 1 MiB, defined at file scope in the library,
+ *   which every GPU that loads the library holds until the process exits.
+ *   Limits: out-degree of s and in-degree of t each <= 65536, else
+ *   MHR_ERANGE; 1 <= K <= MHR_K_MAX; s, t valid and s != t (MHR_EINVAL).
+ *   The first call on each device looks up the device address of that array
+ *   and sets the kernel's shared-memory attribute; make that first call
+ *   before any stream capture.  Every call on a device shares the array and
+ *   it keeps the last call's contents (each call writes every cell it reads),
+ *   so calls that overlap on the GPU (other streams, other threads) race:
+ *   serialise them.
+ */
+mhr_status mhr_topk_paths_noalloc(const mhr_graph* g, uint32_t s, uint32_t t, int32_t K, mhr_path* out,
+                                  int32_t* n_out, void* cuda_stream);
+
 /* Thread-local description of the last non-OK status ("" if none). */
 const char* mhr_last_error(void);
 

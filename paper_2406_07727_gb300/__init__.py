@@ -31,6 +31,7 @@ from ._mhr import (  # noqa: F401
     mhr_last_error,
     mhr_topk_paths,
     mhr_topk_paths_batched,
+    mhr_topk_paths_noalloc,
     mhr_version,
     paths_from_device,
 )

@@ -67,7 +67,7 @@ class Stats(ctypes.Structure):
 
 
 EXPORTS = ("mhr_graph_load", "mhr_graph_free", "mhr_edge_scores", "mhr_topk_paths",
-           "mhr_topk_paths_batched", "mhr_last_error", "mhr_version")
+           "mhr_topk_paths_batched", "mhr_topk_paths_noalloc", "mhr_last_error", "mhr_version")
 
 _lock = threading.Lock()
 _lib = None
@@ -103,6 +103,8 @@ def load_library(build_if_missing: bool = True):
         lib.mhr_topk_paths_batched.restype = ctypes.c_int
         lib.mhr_topk_paths_batched.argtypes = [P, i32, P, P, i32, P, P, ctypes.c_int,
                                                ctypes.POINTER(QueryOpts), ctypes.POINTER(Stats), P]
+        lib.mhr_topk_paths_noalloc.restype = ctypes.c_int
+        lib.mhr_topk_paths_noalloc.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, i32, P, P, P]
         lib.mhr_last_error.restype = ctypes.c_char_p
         lib.mhr_last_error.argtypes = []
         lib.mhr_version.restype = ctypes.c_char_p
@@ -301,6 +303,16 @@ def mhr_topk_paths_batched(g: Graph, S, T, K: int, out=None, n_out=None, opts=No
     if with_stats:
         return out, n_out, st.as_dict()
     return out, n_out
+
+
+def mhr_topk_paths_noalloc(g: Graph, s: int, t: int, K: int, out, n_out, stream=None):
+    """One query into caller-owned device buffers (out: uint8 tensor of K*24
+    bytes, n_out: int32 tensor of 1), allocating nothing; asynchronous."""
+    lib = load_library()
+    if not (_is_torch_cuda(out) and _is_torch_cuda(n_out)):
+        raise ValueError("out and n_out must be device tensors")
+    _check(lib.mhr_topk_paths_noalloc(g.handle, ctypes.c_uint32(int(s)), ctypes.c_uint32(int(t)), int(K),
+                                      _ptr(out), _ptr(n_out), _stream_ptr(stream)))
 
 
 def paths_from_device(buf, K: int) -> np.ndarray:
