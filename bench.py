@@ -50,9 +50,12 @@ WORKLOAD_DESC = ("R-MAT (a,b,c)=(.57,.19,.19) typed KG: 1,000,000 vertices, 20,0
                  "64 edge-biased (s,t) queries per step, K=100, TransE-L1 (gamma=1)")
 DATA = "synthetic: seeded R-MAT typed knowledge graph standing in for WikiKG90Mv2"
 FORM_DESC = {"plain": "plain: batched, every middle edge scored, fp32 screen + fp64 rescoring",
-             "chosen": "chosen: plain + provable bound pruning of middle rows and hits (identical output)"}
-KERNELS_PER_STEP = 16  # k_init, k_expand, 3 scan, k_lists, 3 scan, k_plan, k_near, k_middle,
-#                        k_merge1, k_rescore, k_merge2, k_exact
+             "chosen": "chosen: plain + rows ordered by their score bound, a seed pass per query, provable "
+                       "bound pruning of work items, rows and hits (identical output)"}
+# kernels per step: k_init, k_expand, scan x3, k_lists, scan x3, k_plan, k_order_key,
+# k_order_hist, scan x3, k_order_perm, scan x3, k_near, k_middle (seed), k_middle,
+# k_merge1, k_rescore, k_merge2, k_exact
+KERNELS_PER_STEP = 26
 
 
 def dist_env():
@@ -226,7 +229,7 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
     def make_opts(form):
-        o = {"prune": 0 if form == "plain" else 1}
+        o = {"prune": 0, "order": 0} if form == "plain" else {"prune": 1, "order": 1}
         if args.chunk:
             o["chunk"] = args.chunk
         return o

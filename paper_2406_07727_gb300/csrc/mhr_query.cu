@@ -178,7 +178,11 @@ __global__ void k_init(const PlanDev* __restrict__ P, DevGraph g) {
         P->n_out[q] = 0;
     }
     if (tid < kCntCount) P->counters[tid] = 0ull;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int c = tid; c < P->grid; c += gridDim.x * blockDim.x) P->cursors[c] = 0ull;
+    for (int64_t i = tid; i < 2 * static_cast<int64_t>(nq); i += stride) P->qkey[i] = (i & 1) ? 0u : 0xffffffffu;
+    for (int64_t i = tid; i < P->nhist; i += stride) P->hist[i] = 0u;
+    for (int64_t i = tid; i < P->item_cap; i += stride) P->item_ub[i] = 0u;
 }
 
 // one group of G lanes per slot: fp32 weight, exclusion, run-head flag
@@ -310,28 +314,111 @@ __global__ void __launch_bounds__(1024) k_plan(const PlanDev* __restrict__ P) {
     if (threadIdx.x == 0) P->item_off[nq] = carry;
 }
 
-// near-side entries: (prefix of scan degree, row start)
-__global__ void k_near(const PlanDev* __restrict__ P, DevGraph g) {
-    const int64_t X = P->X, totA = P->totA;
-    const int nq = P->nq;
+// Position of slot x: side, query, region base.  Returns false for slots
+// that are not near-side entries of a valid near list.
+__device__ __forceinline__ bool near_slot(const PlanDev* __restrict__ P, int64_t x, int& q, int64_t& base,
+                                          bool& sideA) {
+    const int64_t totA = P->totA;
+    sideA = x < totA;
+    const int64_t lx = sideA ? x : x - totA;
+    const int64_t* offs = sideA ? P->a_off : P->c_off;
+    q = static_cast<int>(upper_bound_i64(offs, P->nq + 1, lx) - 1);
+    base = sideA ? offs[q] : totA + offs[q];
+    if ((P->dir[q] == 1) != sideA) return false;
+    return x - base < P->near_cnt[q];
+}
+
+// row bound of every near entry, its order key and the per-query key range
+__global__ void k_order_key(const PlanDev* __restrict__ P, DevGraph g) {
+    const int64_t X = P->X;
+    const int order = P->order;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < X; x += stride) {
-        const bool sideA = x < totA;
-        const int64_t lx = sideA ? x : x - totA;
-        const int64_t* offs = sideA ? P->a_off : P->c_off;
-        const int q = static_cast<int>(upper_bound_i64(offs, nq + 1, lx) - 1);
-        if ((P->dir[q] == 1) != sideA) continue;
-        const int64_t base = sideA ? offs[q] : totA + offs[q];
-        if (x - base >= P->near_cnt[q]) continue;
+        P->degv3[x] = 0u;
+        int q;
+        int64_t base;
+        bool sideA;
+        if (!near_slot(P, x, q, base, sideA)) continue;
         const ListEnt e = P->list[x];
-        P->nearP[x] = make_uint2(static_cast<uint32_t>(P->scan2[x] - P->scan2[base]), e.rowstart);
         // any path through this near entry scores (in fp32) at most:
         //   forward  (near = u): maxw1(u) + maxw_out(u) + max_v maxw3(v)
         //   backward (near = v): max_u maxw1(u) + maxw_in(v) + maxw3(v)
         float b;
         if (sideA) b = __fadd_rn(__fadd_rn(e.maxw, g.maxw_out[e.vertex]), key2f(P->qmax[2 * q + 1]));
         else b = __fadd_rn(__fadd_rn(key2f(P->qmax[2 * q]), g.maxw_in[e.vertex]), e.maxw);
+        P->bnat[x] = b;
+        if (order == 0) continue;
+        const uint32_t key = f2key(order == 1 ? b : P->mlp_pred[x]);
+        P->okey[x] = key;
+        atomicMin(&P->qkey[2 * q], key);
+        atomicMax(&P->qkey[2 * q + 1], key);
+    }
+}
+
+// 256 buckets per query, highest keys first
+__device__ __forceinline__ uint32_t order_bucket(uint32_t key, uint32_t kmin, uint32_t kmax) {
+    const uint64_t range = static_cast<uint64_t>(kmax - kmin) + 1;
+    return static_cast<uint32_t>((static_cast<uint64_t>(kmax - key) * 256) / range);
+}
+
+__global__ void k_order_hist(const PlanDev* __restrict__ P) {
+    if (P->order == 0) return;
+    const int64_t X = P->X;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < X; x += stride) {
+        int q;
+        int64_t base;
+        bool sideA;
+        if (!near_slot(P, x, q, base, sideA)) continue;
+        const uint32_t b = order_bucket(P->okey[x], P->qkey[2 * q], P->qkey[2 * q + 1]);
+        P->orank[x] = atomicAdd(&P->hist[static_cast<int64_t>(q) * 256 + b], 1u);
+    }
+}
+
+// ordered position of every near entry
+__global__ void k_order_perm(const PlanDev* __restrict__ P) {
+    const int64_t X = P->X;
+    const int order = P->order;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < X; x += stride) {
+        int q;
+        int64_t base;
+        bool sideA;
+        if (!near_slot(P, x, q, base, sideA)) continue;
+        int64_t pos = x - base;
+        if (order != 0) {
+            const uint32_t b = order_bucket(P->okey[x], P->qkey[2 * q], P->qkey[2 * q + 1]);
+            const int64_t h = static_cast<int64_t>(q) * 256;
+            pos = P->hscan[h + b] - P->hscan[h] + P->orank[x];
+        }
+        P->nperm[base + pos] = static_cast<uint32_t>(x - base);
+        P->degv3[base + pos] = P->list[x].deg;
+    }
+}
+
+// near entries in ordered position: (prefix of scan degree, row start), row
+// bound, and the largest row bound of every work item
+__global__ void k_near(const PlanDev* __restrict__ P, DevGraph g) {
+    const int64_t X = P->X;
+    const int64_t chunk = P->chunk;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < X; x += stride) {
+        int q;
+        int64_t base;
+        bool sideA;
+        if (!near_slot(P, x, q, base, sideA)) continue;
+        const int64_t old = base + P->nperm[x];
+        const ListEnt e = P->list[old];
+        const int64_t pre = P->scan4[x] - P->scan4[base];
+        P->nearP[x] = make_uint2(static_cast<uint32_t>(pre), e.rowstart);
+        const float b = P->bnat[old];
         P->nearB[x] = b;
+        if (P->prune && e.deg > 0) {
+            const uint32_t key = f2key(b);
+            const int64_t i0 = P->item_off[q] + pre / chunk;
+            const int64_t i1 = P->item_off[q] + (pre + e.deg - 1) / chunk;
+            for (int64_t i = i0; i <= i1; ++i) atomicMax(&P->item_ub[i], key);
+        }
     }
 }
 
@@ -541,7 +628,10 @@ __device__ __forceinline__ float hit_w32_f32(const DevGraph& g, NearRow& nr, uin
     return transe ? __fsub_rn(g.gamma32, acc) : acc;
 }
 
-template <int UNROLL>
+// SEED: with bound pruning on, a first launch processes only the first work
+// item of every query (its highest-bound rows when rows are ordered), so the
+// shared K-th score of every query is set before the main launch starts.
+template <int UNROLL, bool SEED>
 __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __restrict__ P, DevGraph g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MidSmem& sm = *reinterpret_cast<MidSmem*>(smem_raw);
@@ -552,8 +642,9 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
     const double two_err = 2.0 * P->err_path;
     const int64_t total_items = P->item_off[nq];
     Hit* hits = P->hits + static_cast<int64_t>(blockIdx.x) * kMaxChunk;
-    unsigned long long n_scanned = 0, n_hits = 0, n_cands = 0, n_paths_w = 0, n_pruned = 0;
+    unsigned long long n_scanned = 0, n_hits = 0, n_cands = 0, n_paths_w = 0, n_pruned = 0, n_skipped = 0;
     const bool prune = P->prune != 0;
+    if (SEED && !prune) return;
 #ifdef MHR_PHASE_TIMING
     // cycles per phase, thread 0: 0 fetch + query switch, 1 item setup, 2 scan, 3 score
     unsigned long long ph[4] = {0, 0, 0, 0};
@@ -585,32 +676,66 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
 
     for (;;) {
         if (threadIdx.x == 0) {
-            // Items are laid out query by query; CTA b owns the contiguous range
-            // [b*N/grid, (b+1)*N/grid) so it meets few queries, then steals from
-            // the following ranges once its own is drained.
             int64_t it = total_items;
-            while (victim < static_cast<int>(gridDim.x)) {
-                // every item taken already: stop probing the other ranges
-                if (victim > 0 && atomicAdd(&P->counters[kCntItem], 0ull) >= static_cast<unsigned long long>(total_items))
-                    break;
-                const int v = (blockIdx.x + victim) % gridDim.x;
-                const int64_t lo = total_items * v / gridDim.x;
-                const int64_t hi = total_items * (v + 1) / gridDim.x;
-                if (lo < hi) {
-                    const int64_t idx = static_cast<int64_t>(atomicAdd(&P->cursors[v], 1ull));
-                    if (lo + idx < hi) {
-                        it = lo + idx;
-                        atomicAdd(&P->counters[kCntItem], 1ull);
-                        break;
+            int iq = -1;
+            for (;;) {
+                it = total_items;
+                if (SEED) {
+                    // one item per query: the first one
+                    if (prune) {
+                        for (;;) {
+                            const int qq = static_cast<int>(atomicAdd(&P->counters[kCntSeed], 1ull));
+                            if (qq >= nq) break;
+                            if (P->item_off[qq + 1] > P->item_off[qq]) {
+                                it = P->item_off[qq];
+                                break;
+                            }
+                        }
+                    }
+                } else {
+                    // Items are laid out query by query; CTA b owns the contiguous
+                    // range [b*N/grid, (b+1)*N/grid) so it meets few queries, then
+                    // steals from the following ranges once its own is drained.
+                    while (victim < static_cast<int>(gridDim.x)) {
+                        // every item taken already: stop probing the other ranges
+                        if (victim > 0 &&
+                            atomicAdd(&P->counters[kCntItem], 0ull) >= static_cast<unsigned long long>(total_items))
+                            break;
+                        const int v = (blockIdx.x + victim) % gridDim.x;
+                        const int64_t lo = total_items * v / gridDim.x;
+                        const int64_t hi = total_items * (v + 1) / gridDim.x;
+                        if (lo < hi) {
+                            const int64_t idx = static_cast<int64_t>(atomicAdd(&P->cursors[v], 1ull));
+                            if (lo + idx < hi) {
+                                it = lo + idx;
+                                atomicAdd(&P->counters[kCntItem], 1ull);
+                                break;
+                            }
+                        }
+                        ++victim;
                     }
                 }
-                ++victim;
+                if (it >= total_items) break;
+                iq = static_cast<int>(upper_bound_i64(P->item_off, nq + 1, it) - 1);
+                // skip without touching the CTA's query state: the query is being
+                // recomputed exactly, the seed launch did this item, or no row of
+                // the item can reach the query's kept band
+                bool skip = atomicOr(&P->dense[iq], 0) != 0;
+                if (!SEED && prune && !skip) {
+                    if (it == P->item_off[iq]) skip = true;
+                    else {
+                        uint32_t gk = atomicOr(&P->thr_g[iq], 0u);
+                        if (iq == sm.q && sm.lt_key > gk) gk = sm.lt_key;
+                        if (gk != 0u && key2f(P->item_ub[it]) < keep_threshold(gk, two_err)) {
+                            skip = true;
+                            ++n_skipped;
+                        }
+                    }
+                }
+                if (!skip) break;
             }
             sm.item = it;
-            if (it < total_items) {
-                const int q = static_cast<int>(upper_bound_i64(P->item_off, nq + 1, it) - 1);
-                sm.skip = q;  // temporarily: the item's query
-            }
+            sm.skip = iq;  // temporarily: the item's query
         }
         __syncthreads();
         const int64_t item = sm.item;
@@ -816,6 +941,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         // G rounds, so every warp keeps H hits' embedding rows in flight.
         const uint16_t* relsrc = sm.dir ? g.rel : g.rrel;
         const ListEnt* nearL = P->list + sm.near_base;
+        const uint32_t* nperm = P->nperm + sm.near_base;
         const float* w1s = P->w32 + sm.a_base;
         const float* w3s = P->w32 + sm.c_base;
         const int G = P->score_width, H = 32 / G;
@@ -846,7 +972,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                         bool alive = false;
                         if (live) {
                             const Hit ht = hits[hi];
-                            const ListEnt ne = nearL[ht.near_k];
+                            const ListEnt ne = nearL[nperm[ht.near_k]];
                             const ListEnt fe = far[ht.far_k];
                             const ListEnt& ea = sm.dir ? ne : fe;  // hop-1 side (u)
                             const ListEnt& ec = sm.dir ? fe : ne;  // hop-3 side (v)
@@ -979,6 +1105,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         atomicAdd(&P->counters[kCntScanned], n_scanned);
         atomicAdd(&P->counters[kCntHits], n_hits);
         atomicAdd(&P->counters[kCntCands], n_cands);
+        if (n_skipped) atomicAdd(&P->counters[kCntSkippedItems], n_skipped);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) n_pruned += __shfl_xor_sync(FULL, n_pruned, o);
@@ -1184,6 +1311,7 @@ __global__ void __launch_bounds__(1024) k_exact(const PlanDev* __restrict__ P, D
         const int64_t s_near = P->s_near[q];
         const uint2* nearP = P->nearP + nb;
         const ListEnt* nearL = P->list + nb;
+        const uint32_t* nperm = P->nperm + nb;  // ordered position -> list entry
         const ListEnt* far = P->list + fb;
         const uint32_t* colsrc = dir ? g.col : g.rcol;
         const uint16_t* relsrc = dir ? g.rel : g.rrel;
@@ -1207,7 +1335,7 @@ __global__ void __launch_bounds__(1024) k_exact(const PlanDev* __restrict__ P, D
                     else b = mid;
                 }
                 if (a < far_cnt && far[a].vertex == x) {
-                    const ListEnt& ne = nearL[lo];
+                    const ListEnt& ne = nearL[nperm[lo]];
                     const ListEnt& fe = far[a];
                     const ListEnt& ea = dir ? ne : fe;
                     const ListEnt& ec = dir ? fe : ne;
@@ -1222,7 +1350,7 @@ __global__ void __launch_bounds__(1024) k_exact(const PlanDev* __restrict__ P, D
             const int nh = sm.hit_cnt;
             int64_t comb = 0;
             if (threadIdx.x < nh) {
-                const ListEnt& ne = nearL[sm.hnk[threadIdx.x]];
+                const ListEnt& ne = nearL[nperm[sm.hnk[threadIdx.x]]];
                 const ListEnt& fe = far[sm.hfk[threadIdx.x]];
                 comb = static_cast<int64_t>(ne.run_len) * fe.run_len;
             }
@@ -1241,7 +1369,7 @@ __global__ void __launch_bounds__(1024) k_exact(const PlanDev* __restrict__ P, D
                         if (sm.hcomb[mid] <= c) lo = mid;
                         else hi = mid;
                     }
-                    const ListEnt& ne = nearL[sm.hnk[lo]];
+                    const ListEnt& ne = nearL[nperm[sm.hnk[lo]]];
                     const ListEnt& fe = far[sm.hfk[lo]];
                     const ListEnt& ea = dir ? ne : fe;
                     const ListEnt& ec = dir ? fe : ne;
@@ -1296,6 +1424,7 @@ struct Plan {
     std::vector<void*> fixed;
     void* slot_mem = nullptr;
     int64_t slot_cap = 0;
+    void* item_mem = nullptr;
     cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
     cudaStream_t cap = nullptr;
     cudaEvent_t h2d_done = nullptr;
@@ -1316,6 +1445,7 @@ struct Plan {
             if (e) cudaEventDestroy(e);
         for (void* p : fixed) cudaFree(p);
         if (slot_mem) cudaFree(slot_mem);
+        if (item_mem) cudaFree(item_mem);
         if (dregion) cudaFree(dregion);
         if (pin) cudaFreeHost(pin);
     }
@@ -1375,7 +1505,8 @@ static size_t merge2_smem_bytes(int band_cap) {
 static mhr_status ensure_slots(Plan* p, int64_t X) {
     if (X <= p->slot_cap && p->slot_mem) return MHR_OK;
     int64_t cap = std::max<int64_t>(X, std::max<int64_t>(p->slot_cap * 2, 1 << 16));
-    // per slot: w32 4, flag 4, degv 4, scan1 8, scan2 8, list 24, nearP 8, nearB 4
+    // per slot: w32 4, flag 4, degv 4, scan1 8, scan2 8, list 24, nearP 8, nearB 4,
+    // okey 4, orank 4, bnat 4, nperm 4, degv3 4, scan4 8, mlp_pred 4
     const size_t a8 = 256;
     size_t o = 0;
     const size_t o_w32 = o; o = align_up(o + 4 * cap, a8);
@@ -1386,6 +1517,13 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
     const size_t o_list = o; o = align_up(o + sizeof(ListEnt) * cap, a8);
     const size_t o_near = o; o = align_up(o + sizeof(uint2) * cap, a8);
     const size_t o_nb = o; o = align_up(o + sizeof(float) * cap, a8);
+    const size_t o_okey = o; o = align_up(o + 4 * cap, a8);
+    const size_t o_orank = o; o = align_up(o + 4 * cap, a8);
+    const size_t o_bnat = o; o = align_up(o + 4 * cap, a8);
+    const size_t o_nperm = o; o = align_up(o + 4 * cap, a8);
+    const size_t o_degv3 = o; o = align_up(o + 4 * cap, a8);
+    const size_t o_s4 = o; o = align_up(o + 8 * (cap + 1), a8);
+    const size_t o_mlp = o; o = align_up(o + 4 * cap, a8);
     void* mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, o);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (frontier slots)");
@@ -1404,6 +1542,13 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
     p->h.list = reinterpret_cast<ListEnt*>(b + o_list);
     p->h.nearP = reinterpret_cast<uint2*>(b + o_near);
     p->h.nearB = reinterpret_cast<float*>(b + o_nb);
+    p->h.okey = reinterpret_cast<uint32_t*>(b + o_okey);
+    p->h.orank = reinterpret_cast<uint32_t*>(b + o_orank);
+    p->h.bnat = reinterpret_cast<float*>(b + o_bnat);
+    p->h.nperm = reinterpret_cast<uint32_t*>(b + o_nperm);
+    p->h.degv3 = reinterpret_cast<uint32_t*>(b + o_degv3);
+    p->h.scan4 = reinterpret_cast<int64_t*>(b + o_s4);
+    p->h.mlp_pred = reinterpret_cast<float*>(b + o_mlp);
     // scan kernels take raw pointers, so a new buffer needs a new capture
     p->drop_graphs();
     return MHR_OK;
@@ -1412,13 +1557,30 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
 // The sequence is captured as three graphs (before, the join, after) so that
 // timing events recorded between their launches on the caller's stream bracket
 // the join kernel exactly.
+static mhr_status ensure_items(Plan* p, int64_t cap) {
+    cap = std::max<int64_t>(cap, 1);
+    if (cap <= p->h.item_cap && p->h.item_ub) return MHR_OK;
+    cap = std::max(cap, 2 * p->h.item_cap);
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, sizeof(uint32_t) * cap);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (work-item bounds)");
+    if (p->item_mem) {
+        cudaDeviceSynchronize();
+        cudaFree(p->item_mem);
+    }
+    p->item_mem = mem;
+    p->h.item_ub = static_cast<uint32_t*>(mem);
+    p->h.item_cap = cap;
+    return MHR_OK;
+}
+
 static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int part) {
     const PlanDev* d = reinterpret_cast<const PlanDev*>(p->dregion);
     const int sms = std::max(1, G->num_sms);
     const DevGraph& g = G->dg;
     const int64_t* nX = reinterpret_cast<const int64_t*>(p->dregion + offsetof(PlanDev, X));
     if (part == 0) {
-        k_init<<<std::max(1, std::min(sms, (p->nq + 255) / 256)), 256, 0, st>>>(d, g);
+        k_init<<<sms * 2, 256, 0, st>>>(d, g);
         k_expand<<<sms * 8, 256, 0, st>>>(d, g);
         cudaError_t e = device_excl_scan<uint32_t>(p->h.flag, nX, p->h.partials, p->h.scan1, st);
         if (e != cudaSuccess) return e;
@@ -1426,9 +1588,18 @@ static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int
         e = device_excl_scan<uint32_t>(p->h.degv, nX, p->h.partials, p->h.scan2, st);
         if (e != cudaSuccess) return e;
         k_plan<<<1, 1024, 0, st>>>(d);
+        k_order_key<<<sms * 4, 256, 0, st>>>(d, g);
+        k_order_hist<<<sms * 4, 256, 0, st>>>(d);
+        const int64_t* nH = reinterpret_cast<const int64_t*>(p->dregion + offsetof(PlanDev, nhist));
+        e = device_excl_scan<uint32_t>(p->h.hist, nH, p->h.partials, p->h.hscan, st);
+        if (e != cudaSuccess) return e;
+        k_order_perm<<<sms * 4, 256, 0, st>>>(d);
+        e = device_excl_scan<uint32_t>(p->h.degv3, nX, p->h.partials, p->h.scan4, st);
+        if (e != cudaSuccess) return e;
         k_near<<<sms * 4, 256, 0, st>>>(d, g);
     } else if (part == 1) {
-        k_middle<kUnroll><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
+        k_middle<kUnroll, true><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
+        k_middle<kUnroll, false><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
     } else {
         k_merge1<<<std::min(p->nq, sms * 2), 1024, 0, st>>>(d);
         k_rescore<<<sms * 4, kRsWarps * 32, 0, st>>>(d, g);
@@ -1513,6 +1684,10 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) 
     if ((rc = plan_alloc(p, &h.item_off, nq + 1)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.thr_g, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.qmax, 2 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.qkey, 2 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.hist, 256 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.hscan, 256 * static_cast<size_t>(nq) + 1)) != MHR_OK) return bail(rc);
+    h.nhist = 256 * static_cast<int64_t>(nq);
     if ((rc = plan_alloc(p, &h.dense, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.pool_cnt, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.band_cnt, nq)) != MHR_OK) return bail(rc);
@@ -1544,8 +1719,11 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) 
         e = cudaEventCreate(&ev);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
     }
-    e = cudaFuncSetAttribute(k_middle<kUnroll>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_middle<kUnroll, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(mid_smem_bytes()));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_middle<kUnroll, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(mid_smem_bytes()));
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaFuncSetAttribute (middle join)"));
     e = cudaFuncSetAttribute(k_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(exact_smem_bytes()));
@@ -1610,9 +1788,20 @@ static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint
     pa[nq] = ta;
     pc[nq] = tc;
     MHR_TRY(ensure_slots(p, ta + tc));
+    // work items per query are at most ceil(S_near / chunk), and S_near is at
+    // most min(E, deg(s) * max out-degree, deg(t) * max in-degree)
+    int64_t icap = 0;
+    for (int q = 0; q < nq; ++q) {
+        const int64_t da = pa[q + 1] - pa[q], dc = pc[q + 1] - pc[q];
+        const int64_t bound = std::min<int64_t>(G->dg.E, std::min(da * G->max_out_deg, dc * G->max_in_deg));
+        icap += (bound + chunk - 1) / chunk;
+    }
+    MHR_TRY(ensure_items(p, icap));
     p->h.X = ta + tc;
     p->h.totA = ta;
     p->h.prune = (opts && opts->prune) ? 1 : 0;
+    p->h.order = opts ? opts->order : 0;
+    if (p->h.order < 0 || p->h.order > 1) return fail(MHR_EINVAL, "opts->order must be 0 (natural) or 1 (bound)");
     std::memcpy(p->pin, &p->h, sizeof(PlanDev));
     MHR_CUDA_TRY(cudaMemcpyAsync(p->dregion, p->pin, L.total, cudaMemcpyHostToDevice, st));
     MHR_CUDA_TRY(cudaEventRecord(p->h2d_done, st));

@@ -57,7 +57,9 @@ enum {
     kCntDense = 5,
     kCntPruned = 6,
     kCntPaths = 7,
-    kCntCount = 8
+    kCntSeed = 8,
+    kCntSkippedItems = 9,
+    kCntCount = 16
 };
 
 // Everything a batch needs, in device memory; kernels take a pointer to it so
@@ -66,6 +68,9 @@ struct PlanDev {
     int32_t nq, K, chunk, sigma;
     int32_t nbw, pq, band_cap, score_width;
     int32_t grid, prune;  // persistent CTAs of the join; bound pruning on/off
+    int32_t order, pad2;  // near-row order: 0 natural, 1 by bound, 2 by learned score
+    int64_t nhist;        // nq * 256 order buckets
+    int64_t item_cap;     // capacity of item_ub
     int64_t X;     // slots = totA + totC
     int64_t totA;  // slots of the hop-1 side
     double err_path;
@@ -83,6 +88,18 @@ struct PlanDev {
     int64_t* scan2;
     uint2* nearP;  // (prefix of scan degree within the query, row start)
     float* nearB;  // upper bound of the fp32 score of any path through a near entry
+    // near-row ordering (slot arrays [X], scans [X+1])
+    uint32_t* okey;     // order key of a near entry (natural position)
+    uint32_t* orank;    // rank inside its bucket
+    float* bnat;        // row bound in natural position
+    uint32_t* nperm;    // ordered position -> dense index of the near entry
+    uint32_t* degv3;    // scan degree in ordered position
+    int64_t* scan4;     // prefix of degv3
+    float* mlp_pred;    // learned order key (order 2)
+    uint32_t* qkey;     // [2 nq] min / max order key per query
+    uint32_t* hist;     // [nq * 256] bucket counts
+    int64_t* hscan;     // [nq * 256 + 1]
+    uint32_t* item_ub;  // [item_cap] key of the largest row bound in a work item
     // per query [nq] (+1 for item_off)
     int32_t* status;
     int32_t* dir;       // 1 = forward (scan out-rows of hop-1 vertices), 0 = backward

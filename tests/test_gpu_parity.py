@@ -139,9 +139,9 @@ def test_topk_golden_batched_and_edge_cases(mhr):
 
 
 # --------------------------------------------------------------------------- random graphs
-@pytest.mark.parametrize("prune", [0, 1])
+@pytest.mark.parametrize("prune,order", [(0, 0), (1, 0), (1, 1), (0, 1)])
 @pytest.mark.parametrize("fn", ["transe", "distmult"])
-def test_topk_random_small_graphs(mhr, fn, prune):
+def test_topk_random_small_graphs(mhr, fn, prune, order):
     rng = np.random.default_rng(101 if fn == "transe" else 202)
     for trial in range(30):
         n = int(rng.integers(8, 300))
@@ -154,11 +154,11 @@ def test_topk_random_small_graphs(mhr, fn, prune):
         S = rng.integers(0, n, nq).astype(np.uint32)
         T = rng.integers(0, n, nq).astype(np.uint32)
         K = int(rng.choice([1, 2, 7, 50, 300]))
-        run_and_compare(mhr, g, S, T, K, fn, opts={"prune": prune})
+        run_and_compare(mhr, g, S, T, K, fn, opts={"prune": prune, "order": order})
 
 
-@pytest.mark.parametrize("prune", [0, 1])
-def test_topk_all_ties_zero_embeddings(mhr, prune):
+@pytest.mark.parametrize("prune,order", [(0, 0), (1, 1)])
+def test_topk_all_ties_zero_embeddings(mhr, prune, order):
     """Every score equal: the order is the id order and the fp32 screen cannot
     separate anything (exercises the tie-heavy exact path)."""
     rng = np.random.default_rng(7)
@@ -167,7 +167,7 @@ def test_topk_all_ties_zero_embeddings(mhr, prune):
         S = rng.integers(0, 200, 10).astype(np.uint32)
         T = rng.integers(0, 200, 10).astype(np.uint32)
         for fn in ("transe", "distmult"):
-            run_and_compare(mhr, g, S, T, int(rng.choice([5, 64, 500])), fn, opts={"prune": prune})
+            run_and_compare(mhr, g, S, T, int(rng.choice([5, 64, 500])), fn, opts={"prune": prune, "order": order})
 
 
 def test_topk_dyadic_many_ties_large_K(mhr):
@@ -179,22 +179,22 @@ def test_topk_dyadic_many_ties_large_K(mhr):
     run_and_compare(mhr, g, S, T, 100, "distmult")
 
 
-@pytest.mark.parametrize("prune", [0, 1])
+@pytest.mark.parametrize("prune,order", [(0, 0), (1, 0), (1, 1)])
 @pytest.mark.parametrize("chunk", [32, 64, 1024, 16384])
-def test_topk_chunk_sizes(mhr, chunk, prune):
+def test_topk_chunk_sizes(mhr, chunk, prune, order):
     """Work items of any size give the same answer (several items per query,
     ragged tails, hub rows split across items)."""
     g = synth.gen_rmat_kg(13, 6000, 120_000, 5, 3, seed=4)
     g.vemb, g.remb = synth.gen_embeddings(g.n, g.R, 16, 0.25, seed=4)
     S, T = synth.queries_edge_biased(g, 20, seed=4)
-    run_and_compare(mhr, g, S, T, 60, "transe", opts={"chunk": chunk, "prune": prune})
+    run_and_compare(mhr, g, S, T, 60, "transe", opts={"chunk": chunk, "prune": prune, "order": order})
 
 
 def test_tiny_workload(mhr):
     """10k vertices / 100k edges Zipf(2.1), d=64 fp32, hub query, K=10 (+ K=100)."""
     g, S, T, K, spec = synth.workload("tiny")
-    for prune in (0, 1):
-        o = {"prune": prune}
+    for prune, order in ((0, 0), (1, 0), (1, 1)):
+        o = {"prune": prune, "order": order}
         run_and_compare(mhr, g, S, T, K, "transe", opts=o)
         run_and_compare(mhr, g, S, T, 100, "transe", opts=o)
         run_and_compare(mhr, g, S, T, K, "distmult", opts=o)
@@ -229,6 +229,7 @@ def test_large_vertex_count_coarse_bitmap(mhr):
     S, T = synth.queries_edge_biased(g, 24, seed=6)
     run_and_compare(mhr, g, S, T, 50, "transe")
     run_and_compare(mhr, g, S, T, 50, "transe", opts={"prune": 1})
+    run_and_compare(mhr, g, S, T, 50, "transe", opts={"prune": 1, "order": 1})
 
 
 def test_device_memory_batched(mhr):
@@ -293,7 +294,7 @@ def test_medium_workload_sampled(mhr):
     g, S, T, K, spec = synth.workload("medium")
     G = mhr.load_kg(g)
     out, n_out = mhr.mhr_topk_paths_batched(G, S, T, K)
-    outp, n_outp, st = mhr.mhr_topk_paths_batched(G, S, T, K, opts={"prune": 1}, with_stats=True)
+    outp, n_outp, st = mhr.mhr_topk_paths_batched(G, S, T, K, opts={"prune": 1, "order": 1}, with_stats=True)
     G.close()
     assert st["pruned_edges"] > 0
     # the pruned form returns byte-identical results for every query
