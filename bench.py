@@ -45,9 +45,17 @@ if ROOT not in sys.path:
 METRIC = "3-hop top-K queries/s on 1 GB300, plain vs chosen form, top-K identical to oracle"
 UNIT = "queries/s"
 WORKLOAD = "medium"
-WORKLOAD_DESC = ("R-MAT (a,b,c)=(.57,.19,.19) typed KG: 1,000,000 vertices, 20,000,000 edges, "
-                 "16 relations, 6 vertex types, d=128 fp32 embeddings ~N(0,1/sqrt(d)); "
-                 "64 edge-biased (s,t) queries per step, K=100, TransE-L1 (gamma=1)")
+WORKLOAD_DESCS = {
+    "medium": ("R-MAT (a,b,c)=(.57,.19,.19) typed KG: 1,000,000 vertices, 20,000,000 edges, "
+               "16 relations, 6 vertex types, d=128 fp32 embeddings ~N(0,1/sqrt(d)); "
+               "64 edge-biased (s,t) queries per step, K=100, TransE-L1 (gamma=1)"),
+    "batching": ("R-MAT (a,b,c)=(.57,.19,.19) typed KG: 10,000,000 vertices, 200,000,000 edges, "
+                 "32 relations, 6 vertex types, d=128 bf16 embeddings ~N(0,1/sqrt(d)); 4,096 queries "
+                 "per step with log-uniform source degree in [1,1e5], K=50, TransE-L1 (gamma=1)"),
+    "tiny": ("Zipf(2.1) typed KG: 10,000 vertices, 100,000 edges, 8 relations, d=64 fp32 ~N(0,1/8); "
+             "one hub query, K=10, TransE-L1"),
+}
+WORKLOAD_DESC = WORKLOAD_DESCS[WORKLOAD]
 DATA = "synthetic: seeded R-MAT typed knowledge graph standing in for WikiKG90Mv2"
 FORM_DESC = {"plain": "plain: batched, every middle edge scored, fp32 screen + fp64 rescoring",
              "chosen": "chosen: plain + rows ordered by their score bound, a seed pass per query, provable "
@@ -70,7 +78,10 @@ def load_workload(rank: int):
     os.environ.setdefault("MHR_SYNTH_CACHE", os.path.join(tempfile.gettempdir(), "mhr_synth_cache"))
     g, S, T, K, spec = synth.workload(WORKLOAD)
     if rank > 0:  # weak scaling: each rank its own 64 queries on the same graph
-        S, T = synth.queries_edge_biased(g, len(S), seed=rank)
+        if WORKLOAD == "batching":
+            S, T = synth.queries_log_degree(g, len(S), seed=rank)
+        else:
+            S, T = synth.queries_edge_biased(g, len(S), seed=rank)
     return g, S, T, K, spec
 
 
@@ -362,9 +373,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--chunk", type=int, default=0, help="middle-join work item size (0 = default)")
+    ap.add_argument("--workload", default="medium", choices=sorted(WORKLOAD_DESCS),
+                    help="medium is the benchmark workload; the others are extra measurements")
     ap.add_argument("--form", default="chosen", choices=["plain", "chosen"],
                     help="plain: every hit scored; chosen: provable bound pruning (same output)")
     args = ap.parse_args()
+    global WORKLOAD, WORKLOAD_DESC
+    WORKLOAD, WORKLOAD_DESC = args.workload, WORKLOAD_DESCS[args.workload]
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

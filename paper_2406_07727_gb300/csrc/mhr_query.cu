@@ -426,6 +426,7 @@ __global__ void k_near(const PlanDev* __restrict__ P, DevGraph g) {
 // the middle join (persistent)
 // ===========================================================================
 constexpr int kRelCacheVecs = 512;  // 8 KB of fp32 relation embeddings
+constexpr int kSeedEdges = 2048;    // edges of each query's highest-bound rows done by the seed launch
 
 struct MidSmem {
     uint32_t bm[kMaxBmWords];
@@ -628,6 +629,21 @@ __device__ __forceinline__ float hit_w32_f32(const DevGraph& g, NearRow& nr, uin
     return transe ? __fsub_rn(g.gamma32, acc) : acc;
 }
 
+// edge range [e0, e1) of a work item in the query's near-edge space; the seed
+// launch does the first kSeedEdges edges of the first item, the main launch the
+// rest of it
+template <bool SEED>
+__device__ __forceinline__ void item_edges(const PlanDev* __restrict__ P, int64_t item, int q, bool prune,
+                                           int64_t& e0, int64_t& e1) {
+    const int64_t s_near = P->s_near[q];
+    e0 = (item - P->item_off[q]) * P->chunk;
+    e1 = min(e0 + static_cast<int64_t>(P->chunk), s_near);
+    if (prune && e0 == 0) {
+        if (SEED) e1 = min(e1, static_cast<int64_t>(kSeedEdges));
+        else e0 = min(e1, static_cast<int64_t>(kSeedEdges));
+    }
+}
+
 // SEED: with bound pruning on, a first launch processes only the first work
 // item of every query (its highest-bound rows when rows are ordered), so the
 // shared K-th score of every query is set before the main launch starts.
@@ -718,11 +734,11 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                 if (it >= total_items) break;
                 iq = static_cast<int>(upper_bound_i64(P->item_off, nq + 1, it) - 1);
                 // skip without touching the CTA's query state: the query is being
-                // recomputed exactly, the seed launch did this item, or no row of
-                // the item can reach the query's kept band
+                // recomputed exactly, the seed launch did all of this item, or no
+                // row of the item can reach the query's kept band
                 bool skip = atomicOr(&P->dense[iq], 0) != 0;
                 if (!SEED && prune && !skip) {
-                    if (it == P->item_off[iq]) skip = true;
+                    if (it == P->item_off[iq] && P->s_near[iq] <= kSeedEdges) skip = true;
                     else {
                         uint32_t gk = atomicOr(&P->thr_g[iq], 0u);
                         if (iq == sm.q && sm.lt_key > gk) gk = sm.lt_key;
@@ -755,15 +771,15 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                 sm.lt_key = gk;
                 sm.thr_keep = keep_threshold(gk, two_err);
             }
-            const int64_t e0 = (item - P->item_off[q]) * P->chunk;
-            const int64_t e1 = min(e0 + static_cast<int64_t>(P->chunk), sm.s_near);
+            int64_t e0, e1;
+            item_edges<SEED>(P, item, q, prune, e0, e1);
             sm.e0 = static_cast<uint32_t>(e0);
             sm.e1 = static_cast<uint32_t>(e1);
             sm.hit_cnt = 0;
         } else if (threadIdx.x == 32 || threadIdx.x == 64) {
             // largest near index whose prefix is <= e (e = e0 or e1 - 1)
-            const int64_t e0 = (item - P->item_off[q]) * P->chunk;
-            const int64_t e1 = min(e0 + static_cast<int64_t>(P->chunk), P->s_near[q]);
+            int64_t e0, e1;
+            item_edges<SEED>(P, item, q, prune, e0, e1);
             const int64_t e = threadIdx.x == 32 ? e0 : e1 - 1;
             const int64_t nb = P->dir[q] ? P->a_off[q] : P->totA + P->c_off[q];
             int lo = 0, hi = P->near_cnt[q];

@@ -348,11 +348,17 @@ def workload(name: str, seed: int = 0, **override):
             return g, z["S"], z["T"], spec["K"], spec
     g, S, T, K, spec = _build_workload(spec, seed)
     if cp is not None:
-        tmp = cp + ".tmp.npz"
-        np.savez(tmp, offsets=g.offsets, cols=g.cols, rels=g.rels, vtypes=g.vtypes, vemb=g.vemb,
-                 remb=g.remb, S=S, T=T)
         import os
-        os.replace(tmp, cp)
+        tmp = cp + ".tmp.npz"
+        try:
+            np.savez(tmp, offsets=g.offsets, cols=g.cols, rels=g.rels, vtypes=g.vtypes, vemb=g.vemb,
+                     remb=g.remb, S=S, T=T)
+            os.replace(tmp, cp)
+        except OSError:  # no room for the cache: keep going without it
+            try:
+                os.unlink(tmp)
+            except OSError:
+                pass
     return g, S, T, K, spec
 
 

@@ -328,3 +328,29 @@ def test_work_counters_match_oracle(mhr):
         assert st["paths"] == paths
         assert st["ms_join"] > 0 and st["ms_device"] >= st["ms_join"]
     G.close()
+
+
+@pytest.mark.slow
+def test_batching_workload_sampled(mhr):
+    """R-MAT 10M vertices / 200M edges, R=32, d=128 bf16, 4,096 queries with
+    log-uniform source degree, K=50: the whole batch in one call (coarse
+    shared-memory bitmap, n > 2^20); the oracle recomputes a sample of queries."""
+    g, S, T, K, spec = synth.workload("batching")
+    G = mhr.load_kg(g)
+    for opts in ({"prune": 0, "order": 0}, {"prune": 1, "order": 1}):
+        out, n_out = mhr.mhr_topk_paths_batched(G, S, T, K, opts=opts)
+        if opts["prune"] == 0:
+            base_out, base_n = out.copy(), n_out.copy()
+        else:
+            assert np.array_equal(base_n, n_out)
+            for q in range(len(S)):
+                assert base_out[q][: base_n[q]].tobytes() == out[q][: n_out[q]].tobytes()
+    G.close()
+    od = g.out_degree()
+    # a sample spanning the source-degree range, bounded so the oracle stays quick
+    order = np.argsort(od[S], kind="stable")
+    sample = order[np.linspace(0, len(S) - 1, 10).astype(int)]
+    sample = [q for q in sample if od[S[q]] <= 20000][:8]
+    want, n_want = oracle.topk_paths_batch(g, S[sample], T[sample], K)
+    for i, q in enumerate(sample):
+        compare_query(base_out[q], int(base_n[q]), want[i, : n_want[i]], ctx=int(q))
