@@ -101,12 +101,29 @@ typedef struct {
     uint16_t r1, r2, r3, pad;
 } mhr_path;
 
+/*
+ * Ordering MLP (device pointers): y = w2 . relu(W1 x + b1) + b2 with x the 256
+ * bfloat16 features [e_a[0:128]; e_b[0:128]] of two vertices (zero-padded when
+ * dim < 128), 256 hidden units.  W1: bfloat16 bits [256 hidden x 256 in],
+ * row-major; b1, w2: float[256]; b2: float[1].
+ */
+typedef struct {
+    const uint16_t* W1;
+    const float* b1;
+    const float* w2;
+    const float* b2;
+} mhr_mlp;
+
 /* Query options; a NULL pointer means all defaults (zeros). */
 typedef struct {
-    int32_t chunk;       /* edges per work item of the middle join; 0 = autotuned/default */
-    int32_t order;       /* 0 = natural order of intermediate vertices */
-    int32_t prune;       /* 0 = no bound pruning */
-    int32_t reserved[5];
+    int32_t chunk;       /* edges per work item of the middle join; 0 = default */
+    int32_t order;       /* order of intermediate vertices: 0 natural, 1 by score
+                            bound, 2 by the learned score of `mlp` */
+    int32_t prune;       /* 1 = skip work items, rows and middle edges whose provable
+                            score bound cannot reach the kept band (same result) */
+    int32_t reserved0;
+    const mhr_mlp* mlp;  /* order == 2 only */
+    int32_t reserved[2];
 } mhr_query_opts;
 
 /* Work counters of the last call (optional output). */
@@ -167,6 +184,48 @@ mhr_status mhr_topk_paths_batched(const mhr_graph* g, int32_t nq, const uint32_t
                                   const uint32_t* t, int32_t K, mhr_path* out, int32_t* n_out,
                                   mhr_mem mem, const mhr_query_opts* opts, mhr_stats* stats,
                                   void* cuda_stream);
+
+/*
+ * Learned ordering (the paper has no learned component; this implements the
+ * ordering proposal of the spec design on top of the exact search).
+ * All arrays are device memory; calls are asynchronous on cuda_stream.
+ *
+ * mhr_training_labels: runs the plain search (no pruning) on nq queries
+ * (s, t: host arrays) and writes, for every intermediate vertex x scanned by
+ * the join that lies on at least one path, one training row: near_v[i] = x,
+ * end_v[i] = the query endpoint on the far side of x (t when x is a hop-1
+ * vertex, s when it is a hop-3 vertex), own[i] = the best fp32 weight of x's
+ * own hop edge, best[i] = the best fp32 path score through x.  At most cap
+ * rows; *n_written (host) = rows written, or the number needed when > cap
+ * (then MHR_ERANGE).  Synchronous.
+ */
+mhr_status mhr_training_labels(const mhr_graph* g, int32_t nq, const uint32_t* s, const uint32_t* t,
+                               int64_t cap, uint32_t* near_v, uint32_t* end_v, float* own, float* best,
+                               int64_t* n_written, void* cuda_stream);
+
+/* X[i] = bfloat16 features [e_va[i][0:128]; e_vb[i][0:128]], X is [n x 256]. */
+mhr_status mhr_mlp_features(const mhr_graph* g, const uint32_t* va, const uint32_t* vb, int64_t n,
+                            uint16_t* X, void* cuda_stream);
+
+/* y[i] = MLP(X[i]); z1 (optional, [n x 256]) receives W1 x + b1. */
+mhr_status mhr_mlp_forward(const mhr_mlp* m, const uint16_t* X, int64_t n, float* y, float* z1,
+                           void* cuda_stream);
+
+/*
+ * Gradients of mean_i (y[i] - target[i])^2 for the y, z1 of mhr_mlp_forward:
+ * grads = [dW1 (256x256 row-major) | db1 (256) | dw2 (256) | db2 (1)] fp32;
+ * work: n x 256 floats of scratch; loss (optional, device float).
+ */
+mhr_status mhr_mlp_backward(const mhr_mlp* m, const uint16_t* X, int64_t n, const float* target,
+                            const float* y, const float* z1, float* work, float* grads, float* loss,
+                            void* cuda_stream);
+
+/* One Adam step on count parameters (step >= 1, bias-corrected). */
+mhr_status mhr_mlp_adam(float* params, const float* grads, float* m1, float* m2, int64_t count,
+                        float lr, float beta1, float beta2, float eps, int32_t step, void* cuda_stream);
+
+/* dst[i] = bfloat16(src[i]) (round to nearest even). */
+mhr_status mhr_mlp_to_bf16(const float* src, uint16_t* dst, int64_t count, void* cuda_stream);
 
 /*
  * mhr_topk_paths_noalloc - one query, like mhr_topk_paths, for callers that

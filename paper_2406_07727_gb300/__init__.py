@@ -32,8 +32,17 @@ from ._mhr import (  # noqa: F401
     mhr_topk_paths,
     mhr_topk_paths_batched,
     mhr_topk_paths_noalloc,
+    mhr_training_labels,
+    mhr_mlp_features,
+    mhr_mlp_forward,
+    mhr_mlp_backward,
+    mhr_mlp_adam,
+    mhr_mlp_to_bf16,
+    MLP,
     mhr_version,
     paths_from_device,
 )
+
+from .learn import OrderingMLP, train_ordering_mlp  # noqa: E402,F401
 
 load_library()

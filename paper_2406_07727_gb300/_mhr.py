@@ -50,9 +50,15 @@ class GraphDesc(ctypes.Structure):
                 ("gamma", ctypes.c_double)]
 
 
+class MLP(ctypes.Structure):
+    _fields_ = [("W1", ctypes.c_void_p), ("b1", ctypes.c_void_p), ("w2", ctypes.c_void_p),
+                ("b2", ctypes.c_void_p)]
+
+
 class QueryOpts(ctypes.Structure):
     _fields_ = [("chunk", ctypes.c_int32), ("order", ctypes.c_int32), ("prune", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("reserved0", ctypes.c_int32), ("mlp", ctypes.POINTER(MLP)),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Stats(ctypes.Structure):
@@ -67,7 +73,9 @@ class Stats(ctypes.Structure):
 
 
 EXPORTS = ("mhr_graph_load", "mhr_graph_free", "mhr_edge_scores", "mhr_topk_paths",
-           "mhr_topk_paths_batched", "mhr_topk_paths_noalloc", "mhr_last_error", "mhr_version")
+           "mhr_topk_paths_batched", "mhr_topk_paths_noalloc", "mhr_training_labels",
+           "mhr_mlp_features", "mhr_mlp_forward", "mhr_mlp_backward", "mhr_mlp_adam",
+           "mhr_mlp_to_bf16", "mhr_last_error", "mhr_version")
 
 _lock = threading.Lock()
 _lib = None
@@ -103,6 +111,19 @@ def load_library(build_if_missing: bool = True):
         lib.mhr_topk_paths_batched.restype = ctypes.c_int
         lib.mhr_topk_paths_batched.argtypes = [P, i32, P, P, i32, P, P, ctypes.c_int,
                                                ctypes.POINTER(QueryOpts), ctypes.POINTER(Stats), P]
+        lib.mhr_training_labels.restype = ctypes.c_int
+        lib.mhr_training_labels.argtypes = [P, i32, P, P, i64, P, P, P, P, ctypes.POINTER(i64), P]
+        lib.mhr_mlp_features.restype = ctypes.c_int
+        lib.mhr_mlp_features.argtypes = [P, P, P, i64, P, P]
+        lib.mhr_mlp_forward.restype = ctypes.c_int
+        lib.mhr_mlp_forward.argtypes = [ctypes.POINTER(MLP), P, i64, P, P, P]
+        lib.mhr_mlp_backward.restype = ctypes.c_int
+        lib.mhr_mlp_backward.argtypes = [ctypes.POINTER(MLP), P, i64, P, P, P, P, P, P, P]
+        lib.mhr_mlp_adam.restype = ctypes.c_int
+        lib.mhr_mlp_adam.argtypes = [P, P, P, P, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float, i32, P]
+        lib.mhr_mlp_to_bf16.restype = ctypes.c_int
+        lib.mhr_mlp_to_bf16.argtypes = [P, P, i64, P]
         lib.mhr_topk_paths_noalloc.restype = ctypes.c_int
         lib.mhr_topk_paths_noalloc.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, i32, P, P, P]
         lib.mhr_last_error.restype = ctypes.c_char_p
@@ -169,7 +190,11 @@ def _opts(opts) -> Optional[QueryOpts]:
         return opts
     o = QueryOpts()
     for k, v in dict(opts).items():
-        setattr(o, k, int(v))
+        if k == "mlp":
+            o._mlp_keep = v if isinstance(v, MLP) else v.struct()
+            o.mlp = ctypes.pointer(o._mlp_keep)
+        else:
+            setattr(o, k, int(v))
     return o
 
 
@@ -313,6 +338,60 @@ def mhr_topk_paths_noalloc(g: Graph, s: int, t: int, K: int, out, n_out, stream=
         raise ValueError("out and n_out must be device tensors")
     _check(lib.mhr_topk_paths_noalloc(g.handle, ctypes.c_uint32(int(s)), ctypes.c_uint32(int(t)), int(K),
                                       _ptr(out), _ptr(n_out), _stream_ptr(stream)))
+
+
+# --------------------------------------------------------------------------- learned ordering
+def mhr_training_labels(g: Graph, S, T, cap: int, stream=None):
+    """Plain search on (S, T) (host arrays); returns device tensors
+    (near_v, end_v, own, best) of the rows written."""
+    import torch
+    lib = load_library()
+    S, T = _host(S, np.uint32), _host(T, np.uint32)
+    dev = torch.device("cuda")
+    near_v = torch.empty(cap, dtype=torch.int32, device=dev)
+    end_v = torch.empty(cap, dtype=torch.int32, device=dev)
+    own = torch.empty(cap, dtype=torch.float32, device=dev)
+    best = torch.empty(cap, dtype=torch.float32, device=dev)
+    n = ctypes.c_int64(0)
+    _check(lib.mhr_training_labels(g.handle, len(S), _ptr(S), _ptr(T), int(cap), _ptr(near_v), _ptr(end_v),
+                                   _ptr(own), _ptr(best), ctypes.byref(n), _stream_ptr(stream)))
+    k = n.value
+    return near_v[:k], end_v[:k], own[:k], best[:k]
+
+
+def mhr_mlp_features(g: Graph, va, vb, X=None, stream=None):
+    import torch
+    n = int(va.shape[0])
+    if X is None:
+        X = torch.empty((n, 256), dtype=torch.int16, device=va.device)
+    _check(load_library().mhr_mlp_features(g.handle, _ptr(va), _ptr(vb), n, _ptr(X), _stream_ptr(stream)))
+    return X
+
+
+def mhr_mlp_forward(m, X, y=None, z1=None, stream=None):
+    import torch
+    n = int(X.shape[0])
+    if y is None:
+        y = torch.empty(n, dtype=torch.float32, device=X.device)
+    st = m if isinstance(m, MLP) else m.struct()
+    _check(load_library().mhr_mlp_forward(ctypes.byref(st), _ptr(X), n, _ptr(y), _ptr(z1), _stream_ptr(stream)))
+    return y
+
+
+def mhr_mlp_backward(m, X, target, y, z1, work, grads, loss=None, stream=None):
+    st = m if isinstance(m, MLP) else m.struct()
+    _check(load_library().mhr_mlp_backward(ctypes.byref(st), _ptr(X), int(X.shape[0]), _ptr(target), _ptr(y),
+                                           _ptr(z1), _ptr(work), _ptr(grads), _ptr(loss), _stream_ptr(stream)))
+
+
+def mhr_mlp_adam(params, grads, m1, m2, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load_library().mhr_mlp_adam(_ptr(params), _ptr(grads), _ptr(m1), _ptr(m2), int(params.numel()),
+                                       float(lr), float(beta1), float(beta2), float(eps), int(step),
+                                       _stream_ptr(stream)))
+
+
+def mhr_mlp_to_bf16(src, dst, stream=None):
+    _check(load_library().mhr_mlp_to_bf16(_ptr(src), _ptr(dst), int(src.numel()), _stream_ptr(stream)))
 
 
 def paths_from_device(buf, K: int) -> np.ndarray:

@@ -18,6 +18,7 @@
 static_assert(sizeof(mhr_graph_desc) == 104, "mhr_graph_desc layout");
 static_assert(sizeof(mhr_path) == 24, "mhr_path layout");
 static_assert(sizeof(mhr_query_opts) == 32, "mhr_query_opts layout");
+static_assert(sizeof(mhr_mlp) == 32, "mhr_mlp layout");
 static_assert(sizeof(mhr_stats) == 80, "mhr_stats layout");
 
 namespace mhr {

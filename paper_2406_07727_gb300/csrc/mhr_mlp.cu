@@ -1,0 +1,234 @@
+// Ordering MLP: forward (tensor cores), backward and Adam kernels, feature
+// gathering, and their C ABI.  The network orders intermediate vertices so
+// the K-th-score threshold of a query tightens early; it never decides what is
+// pruned (that is left to provable bounds), so it cannot change any result.
+#include <cuda_runtime.h>
+
+#include "mhr_internal.cuh"
+#include "mhr_mlp.cuh"
+
+namespace mhr {
+
+constexpr int kMlpParams = kMlpHid * kMlpIn + kMlpHid + kMlpHid + 1;  // W1, b1, w2, b2
+
+__global__ void __launch_bounds__(kMlpThreads) k_mlp_forward_dense(MlpDev m, const uint16_t* __restrict__ X, int64_t n,
+                                                                   float* __restrict__ y, float* __restrict__ z1) {
+    __shared__ float part[kMlpRows][4];
+    const uint32_t* Xw = reinterpret_cast<const uint32_t*>(X);
+    for (int64_t t0 = static_cast<int64_t>(blockIdx.x) * kMlpRows; t0 < n; t0 += static_cast<int64_t>(gridDim.x) * kMlpRows) {
+        auto a_pair = [&](int r, int k) -> uint32_t {
+            const int64_t row = t0 + r;
+            return row < n ? __ldg(Xw + (row * kMlpIn + k) / 2) : 0u;
+        };
+        auto store_y = [&](int r, float v) {
+            if (t0 + r < n) y[t0 + r] = v;
+        };
+        auto store_z = [&](int r, int c, float v) {
+            if (t0 + r < n) z1[(t0 + r) * kMlpHid + c] = v;
+        };
+        mlp_tile(m, a_pair, store_y, store_z, z1 != nullptr, part);
+    }
+}
+
+__global__ void k_mlp_features(DevGraph g, const uint32_t* __restrict__ va, const uint32_t* __restrict__ vb, int64_t n,
+                               uint16_t* __restrict__ X) {
+    uint32_t* Xw = reinterpret_cast<uint32_t*>(X);
+    const int64_t total = n * (kMlpIn / 2);
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total; i += stride) {
+        const int64_t r = i / (kMlpIn / 2);
+        const int k = static_cast<int>(i - r * (kMlpIn / 2)) * 2;
+        Xw[i] = feature_pair(g, va[r], vb[r], k);
+    }
+}
+
+// dZ[r][c] = (z[r][c] > 0) * dy[r] * w2[c],  dy[r] = 2 (y[r] - t[r]) / n
+__global__ void k_mlp_bwd_rows(const float* __restrict__ w2, const float* __restrict__ y,
+                               const float* __restrict__ tgt, const float* __restrict__ z1, int64_t n,
+                               float* __restrict__ dz) {
+    const int64_t total = n * kMlpHid;
+    const float inv = 2.0f / static_cast<float>(n);
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total; i += stride) {
+        const int64_t r = i / kMlpHid;
+        const int c = static_cast<int>(i - r * kMlpHid);
+        const float dy = (y[r] - tgt[r]) * inv;
+        dz[i] = z1[i] > 0.f ? dy * w2[c] : 0.f;
+    }
+}
+
+// column sums in a fixed order: db1[c] = sum_r dZ[r][c], dw2[c] = sum_r
+// relu(z[r][c]) dy[r]; block 0 also db2 = sum_r dy[r] and the loss
+__global__ void __launch_bounds__(256) k_mlp_bwd_cols(const float* __restrict__ y, const float* __restrict__ tgt,
+                                                      const float* __restrict__ z1, const float* __restrict__ dz,
+                                                      int64_t n, float* __restrict__ grads,
+                                                      float* __restrict__ loss) {
+    __shared__ float s1[8][32], s2[8][32];
+    const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int grp = threadIdx.x >> 5;
+    const float inv = 2.0f / static_cast<float>(n);
+    float a = 0.f, b = 0.f;
+    for (int64_t r = grp; r < n; r += 8) {
+        const float dy = (y[r] - tgt[r]) * inv;
+        a += dz[r * kMlpHid + c];
+        b += fmaxf(z1[r * kMlpHid + c], 0.f) * dy;
+    }
+    s1[grp][threadIdx.x & 31] = a;
+    s2[grp][threadIdx.x & 31] = b;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float sa = 0.f, sb = 0.f;
+        for (int k = 0; k < 8; ++k) {
+            sa += s1[k][threadIdx.x];
+            sb += s2[k][threadIdx.x];
+        }
+        grads[kMlpHid * kMlpIn + c] = sa;            // db1
+        grads[kMlpHid * kMlpIn + kMlpHid + c] = sb;  // dw2
+    }
+    if (blockIdx.x == 0) {
+        __syncthreads();
+        // db2 and the loss, fixed order
+        float d = 0.f, l = 0.f;
+        for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+            const float e = y[r] - tgt[r];
+            d += e * inv;
+            l += e * e;
+        }
+        s1[threadIdx.x >> 5][threadIdx.x & 31] = d;
+        s2[threadIdx.x >> 5][threadIdx.x & 31] = l;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float sd = 0.f, sl = 0.f;
+            for (int k = 0; k < 256; ++k) {
+                sd += s1[k >> 5][k & 31];
+                sl += s2[k >> 5][k & 31];
+            }
+            grads[kMlpHid * kMlpIn + 2 * kMlpHid] = sd;  // db2
+            if (loss) *loss = sl / static_cast<float>(n);
+        }
+    }
+}
+
+// dW1[o][i] = sum_r dZ[r][o] X[r][i]; 64 x 64 output tile per block
+__global__ void __launch_bounds__(256) k_mlp_dw1(const float* __restrict__ dz, const uint16_t* __restrict__ X,
+                                                 int64_t n, float* __restrict__ grads) {
+    __shared__ float sz[32][65], sx[32][65];
+    const int o0 = blockIdx.y * 64, i0 = blockIdx.x * 64;
+    const int to = (threadIdx.x >> 4) * 4, ti = (threadIdx.x & 15) * 4;
+    float acc[4][4] = {};
+    for (int64_t rb = 0; rb < n; rb += 32) {
+        for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
+            const int rr = e >> 6, cc = e & 63;
+            const int64_t r = rb + rr;
+            sz[rr][cc] = r < n ? dz[r * kMlpHid + o0 + cc] : 0.f;
+            sx[rr][cc] = r < n ? __bfloat162float(__ushort_as_bfloat16(X[r * kMlpIn + i0 + cc])) : 0.f;
+        }
+        __syncthreads();
+        for (int rr = 0; rr < 32; ++rr) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += sz[rr][to + a] * sx[rr][ti + b];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) grads[(o0 + to + a) * kMlpIn + i0 + ti + b] = acc[a][b];
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m1,
+                       float* __restrict__ m2, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                       float c2) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+        const float g = gr[i];
+        const float a = b1 * m1[i] + (1.f - b1) * g;
+        const float b = b2 * m2[i] + (1.f - b2) * g * g;
+        m1[i] = a;
+        m2[i] = b;
+        p[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+    }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ src, uint16_t* __restrict__ dst, int64_t n) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride)
+        dst[i] = __bfloat16_as_ushort(__float2bfloat16_rn(src[i]));
+}
+
+static MlpDev to_dev(const mhr_mlp* m) {
+    MlpDev d;
+    d.W1 = m->W1;
+    d.b1 = m->b1;
+    d.w2 = m->w2;
+    d.b2 = m->b2;
+    return d;
+}
+
+static mhr_status check_mlp(const mhr_mlp* m) {
+    if (!m || !m->W1 || !m->b1 || !m->w2 || !m->b2) return fail(MHR_EINVAL, "MLP weights are incomplete");
+    return MHR_OK;
+}
+
+}  // namespace mhr
+
+using namespace mhr;
+
+extern "C" mhr_status mhr_mlp_features(const mhr_graph* g, const uint32_t* va, const uint32_t* vb, int64_t n,
+                                       uint16_t* X, void* cuda_stream) {
+    MHR_TRY(check_graph(g));
+    if (n < 0 || (n && (!va || !vb || !X))) return fail(MHR_EINVAL, "bad feature arguments");
+    if (!n) return MHR_OK;
+    k_mlp_features<<<std::max(1, g->num_sms) * 4, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(g->dg, va, vb, n, X);
+    MHR_CUDA_TRY(cudaGetLastError());
+    return MHR_OK;
+}
+
+extern "C" mhr_status mhr_mlp_forward(const mhr_mlp* m, const uint16_t* X, int64_t n, float* y, float* z1,
+                                      void* cuda_stream) {
+    MHR_TRY(check_mlp(m));
+    if (n < 0 || (n && (!X || !y))) return fail(MHR_EINVAL, "bad forward arguments");
+    if (!n) return MHR_OK;
+    const int64_t tiles = (n + kMlpRows - 1) / kMlpRows;
+    const int grid = static_cast<int>(std::min<int64_t>(tiles, std::max(1, device_sm_count()) * 8));
+    k_mlp_forward_dense<<<grid, kMlpThreads, 0, static_cast<cudaStream_t>(cuda_stream)>>>(to_dev(m), X, n, y, z1);
+    MHR_CUDA_TRY(cudaGetLastError());
+    return MHR_OK;
+}
+
+extern "C" mhr_status mhr_mlp_backward(const mhr_mlp* m, const uint16_t* X, int64_t n, const float* target,
+                                       const float* y, const float* z1, float* work, float* grads, float* loss,
+                                       void* cuda_stream) {
+    MHR_TRY(check_mlp(m));
+    if (n < 1 || !X || !target || !y || !z1 || !work || !grads) return fail(MHR_EINVAL, "bad backward arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int sms = std::max(1, device_sm_count());
+    k_mlp_bwd_rows<<<sms * 4, 256, 0, st>>>(m->w2, y, target, z1, n, work);
+    k_mlp_bwd_cols<<<kMlpHid / 32, 256, 0, st>>>(y, target, z1, work, n, grads, loss);
+    k_mlp_dw1<<<dim3(kMlpIn / 64, kMlpHid / 64), 256, 0, st>>>(work, X, n, grads);
+    MHR_CUDA_TRY(cudaGetLastError());
+    return MHR_OK;
+}
+
+extern "C" mhr_status mhr_mlp_adam(float* params, const float* grads, float* m1, float* m2, int64_t count, float lr,
+                                   float beta1, float beta2, float eps, int32_t step, void* cuda_stream) {
+    if (count < 0 || (count && (!params || !grads || !m1 || !m2)) || step < 1)
+        return fail(MHR_EINVAL, "bad Adam arguments");
+    if (!count) return MHR_OK;
+    const float c1 = 1.f - powf(beta1, static_cast<float>(step));
+    const float c2 = 1.f - powf(beta2, static_cast<float>(step));
+    k_adam<<<std::max(1, device_sm_count()) * 4, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
+        params, grads, m1, m2, count, lr, beta1, beta2, eps, c1, c2);
+    MHR_CUDA_TRY(cudaGetLastError());
+    return MHR_OK;
+}
+
+extern "C" mhr_status mhr_mlp_to_bf16(const float* src, uint16_t* dst, int64_t count, void* cuda_stream) {
+    if (count < 0 || (count && (!src || !dst))) return fail(MHR_EINVAL, "bad conversion arguments");
+    if (!count) return MHR_OK;
+    k_to_bf16<<<std::max(1, device_sm_count()) * 4, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(src, dst, count);
+    MHR_CUDA_TRY(cudaGetLastError());
+    return MHR_OK;
+}

@@ -328,6 +328,43 @@ __device__ __forceinline__ bool near_slot(const PlanDev* __restrict__ P, int64_t
     return x - base < P->near_cnt[q];
 }
 
+// Learned order key of every near entry (order 2): the MLP predicts the best
+// completion of a path through the entry from [e_entry; e_far endpoint]; the
+// key adds the entry's own best hop weight.  Tiles of 32 slots.
+__global__ void __launch_bounds__(kMlpThreads) k_mlp_keys(const PlanDev* __restrict__ P, DevGraph g) {
+    if (P->order != 2) return;
+    __shared__ float part[kMlpRows][4];
+    __shared__ uint32_t va[kMlpRows], vb[kMlpRows];
+    __shared__ float own[kMlpRows];
+    __shared__ int ok[kMlpRows];
+    const int64_t X = P->X;
+    for (int64_t t0 = static_cast<int64_t>(blockIdx.x) * kMlpRows; t0 < X; t0 += static_cast<int64_t>(gridDim.x) * kMlpRows) {
+        if (threadIdx.x < kMlpRows) {
+            const int64_t x = t0 + threadIdx.x;
+            int q = 0;
+            int64_t base = 0;
+            bool sideA = true;
+            const bool v = x < X && near_slot(P, x, q, base, sideA);
+            ok[threadIdx.x] = v;
+            va[threadIdx.x] = vb[threadIdx.x] = 0u;
+            own[threadIdx.x] = 0.f;
+            if (v) {
+                const ListEnt e = P->list[x];
+                va[threadIdx.x] = e.vertex;
+                vb[threadIdx.x] = sideA ? P->T[q] : P->S[q];
+                own[threadIdx.x] = e.maxw;
+            }
+        }
+        __syncthreads();
+        auto a_pair = [&](int r, int k) -> uint32_t { return ok[r] ? feature_pair(g, va[r], vb[r], k) : 0u; };
+        auto store_y = [&](int r, float y) {
+            if (ok[r]) P->mlp_pred[t0 + r] = own[r] + y;
+        };
+        auto store_z = [&](int, int, float) {};
+        mlp_tile(P->mlp, a_pair, store_y, store_z, false, part);
+    }
+}
+
 // row bound of every near entry, its order key and the per-query key range
 __global__ void k_order_key(const PlanDev* __restrict__ P, DevGraph g) {
     const int64_t X = P->X;
@@ -335,6 +372,7 @@ __global__ void k_order_key(const PlanDev* __restrict__ P, DevGraph g) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < X; x += stride) {
         P->degv3[x] = 0u;
+        P->ubest[x] = 0u;
         int q;
         int64_t base;
         bool sideA;
@@ -966,7 +1004,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         bool loaded = false;
         unsigned pend = 0;         // lanes whose hit still has combinations to expand
         uint32_t slice = 0;        // this lane's next combination
-        uint32_t hu = 0, hv = 0, hr2 = 0, has = 0, hal = 0, hcs = 0, hcl = 0;
+        uint32_t hu = 0, hv = 0, hr2 = 0, has = 0, hal = 0, hcs = 0, hcl = 0, hnk = 0;
         float hw2 = 0.f;
         NearRow nrow;
         nrow.id = 0xffffffffu;
@@ -988,6 +1026,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                         bool alive = false;
                         if (live) {
                             const Hit ht = hits[hi];
+                            hnk = ht.near_k;
                             const ListEnt ne = nearL[nperm[ht.near_k]];
                             const ListEnt fe = far[ht.far_k];
                             const ListEnt& ea = sm.dir ? ne : fe;  // hop-1 side (u)
@@ -1051,6 +1090,8 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                         }
                         hw2 = w2m;
                         const float smax = __fadd_rn(__fadd_rn(mw1, hw2), mw3);
+                        // training labels (plain runs only): best path score through the near entry
+                        if (P->label && live2) atomicMax(&P->ubest[sm.near_base + hnk], f2key(smax));
                         pend = __ballot_sync(FULL, live2 && smax >= thr);
                         loaded = true;
                         slice = 0;
@@ -1428,6 +1469,30 @@ __global__ void __launch_bounds__(1024) k_exact(const PlanDev* __restrict__ P, D
     }
 }
 
+// training rows from a label run (one per near entry that lies on a path)
+__global__ void k_dump_labels(const PlanDev* __restrict__ P, int64_t cap, uint32_t* __restrict__ near_v,
+                              uint32_t* __restrict__ end_v, float* __restrict__ own, float* __restrict__ best,
+                              unsigned long long* __restrict__ count) {
+    const int64_t X = P->X;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < X; x += stride) {
+        int q;
+        int64_t base;
+        bool sideA;
+        if (!near_slot(P, x, q, base, sideA)) continue;
+        const uint32_t k = P->ubest[x];
+        if (k == 0u) continue;
+        const ListEnt e = P->list[base + P->nperm[x]];
+        const unsigned long long i = atomicAdd(count, 1ull);
+        if (static_cast<int64_t>(i) < cap) {
+            near_v[i] = e.vertex;
+            end_v[i] = sideA ? P->T[q] : P->S[q];
+            own[i] = e.maxw;
+            best[i] = key2f(k);
+        }
+    }
+}
+
 // ===========================================================================
 // host side: plans (buffers + captured graph) per (nq, K, chunk)
 // ===========================================================================
@@ -1540,6 +1605,7 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
     const size_t o_degv3 = o; o = align_up(o + 4 * cap, a8);
     const size_t o_s4 = o; o = align_up(o + 8 * (cap + 1), a8);
     const size_t o_mlp = o; o = align_up(o + 4 * cap, a8);
+    const size_t o_ub = o; o = align_up(o + 4 * cap, a8);
     void* mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, o);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (frontier slots)");
@@ -1565,6 +1631,7 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
     p->h.degv3 = reinterpret_cast<uint32_t*>(b + o_degv3);
     p->h.scan4 = reinterpret_cast<int64_t*>(b + o_s4);
     p->h.mlp_pred = reinterpret_cast<float*>(b + o_mlp);
+    p->h.ubest = reinterpret_cast<uint32_t*>(b + o_ub);
     // scan kernels take raw pointers, so a new buffer needs a new capture
     p->drop_graphs();
     return MHR_OK;
@@ -1604,6 +1671,7 @@ static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int
         e = device_excl_scan<uint32_t>(p->h.degv, nX, p->h.partials, p->h.scan2, st);
         if (e != cudaSuccess) return e;
         k_plan<<<1, 1024, 0, st>>>(d);
+        k_mlp_keys<<<sms * 8, kMlpThreads, 0, st>>>(d, g);
         k_order_key<<<sms * 4, 256, 0, st>>>(d, g);
         k_order_hist<<<sms * 4, 256, 0, st>>>(d);
         const int64_t* nH = reinterpret_cast<const int64_t*>(p->dregion + offsetof(PlanDev, nhist));
@@ -1772,7 +1840,7 @@ static mhr_status get_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) {
 }
 
 static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint32_t* hT, int K,
-                            const mhr_query_opts* opts, cudaStream_t st, Plan** plan_out) {
+                            const mhr_query_opts* opts, cudaStream_t st, Plan** plan_out, bool label = false) {
     int chunk = (opts && opts->chunk > 0) ? opts->chunk : kDefaultChunk;
     if (chunk > kMaxChunk || chunk < 32 || (chunk & 31))
         return fail(MHR_EINVAL, "opts->chunk must be a multiple of 32 in [32, 16384]");
@@ -1817,7 +1885,18 @@ static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint
     p->h.totA = ta;
     p->h.prune = (opts && opts->prune) ? 1 : 0;
     p->h.order = opts ? opts->order : 0;
-    if (p->h.order < 0 || p->h.order > 1) return fail(MHR_EINVAL, "opts->order must be 0 (natural) or 1 (bound)");
+    if (p->h.order < 0 || p->h.order > 2) return fail(MHR_EINVAL, "opts->order must be 0, 1 or 2");
+    p->h.mlp = MlpDev{};
+    if (p->h.order == 2) {
+        const mhr_mlp* m = opts->mlp;
+        if (!m || !m->W1 || !m->b1 || !m->w2 || !m->b2) return fail(MHR_EINVAL, "order 2 needs opts->mlp weights");
+        p->h.mlp.W1 = m->W1;
+        p->h.mlp.b1 = m->b1;
+        p->h.mlp.w2 = m->w2;
+        p->h.mlp.b2 = m->b2;
+    }
+    p->h.label = label ? 1 : 0;
+    if (label && (p->h.prune || p->h.order)) return fail(MHR_EINVAL, "label runs use the plain search");
     std::memcpy(p->pin, &p->h, sizeof(PlanDev));
     MHR_CUDA_TRY(cudaMemcpyAsync(p->dregion, p->pin, L.total, cudaMemcpyHostToDevice, st));
     MHR_CUDA_TRY(cudaEventRecord(p->h2d_done, st));
@@ -1890,6 +1969,30 @@ extern "C" mhr_status mhr_topk_paths_batched(const mhr_graph* gc, int32_t nq, co
         *stats = mhr_stats{};
         MHR_TRY(read_stats(p, st, stats));
     }
+    return MHR_OK;
+}
+
+extern "C" mhr_status mhr_training_labels(const mhr_graph* gc, int32_t nq, const uint32_t* s, const uint32_t* t,
+                                          int64_t cap, uint32_t* near_v, uint32_t* end_v, float* own, float* best,
+                                          int64_t* n_written, void* cuda_stream) {
+    MHR_TRY(check_graph(gc));
+    mhr_graph* G = const_cast<mhr_graph*>(gc);
+    if (nq < 1 || !s || !t || !n_written || cap < 0 || (cap && (!near_v || !end_v || !own || !best)))
+        return fail(MHR_EINVAL, "bad training-label arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    Plan* p = nullptr;
+    mhr_query_opts plain{};
+    MHR_TRY(run_batch(G, nq, s, t, 1, &plain, st, &p, true));
+    unsigned long long* cnt = p->h.counters + kCntLabels;
+    MHR_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+    k_dump_labels<<<std::max(1, G->num_sms) * 4, 256, 0, st>>>(reinterpret_cast<const PlanDev*>(p->dregion), cap,
+                                                               near_v, end_v, own, best, cnt);
+    MHR_CUDA_TRY(cudaGetLastError());
+    unsigned long long h = 0;
+    MHR_CUDA_TRY(cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, st));
+    MHR_CUDA_TRY(cudaStreamSynchronize(st));
+    *n_written = static_cast<int64_t>(h);
+    if (static_cast<int64_t>(h) > cap) return fail(MHR_ERANGE, "more training rows than cap");
     return MHR_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "mhr_internal.cuh"
+#include "mhr_mlp.cuh"
 
 namespace mhr {
 
@@ -59,6 +60,7 @@ enum {
     kCntPaths = 7,
     kCntSeed = 8,
     kCntSkippedItems = 9,
+    kCntLabels = 10,
     kCntCount = 16
 };
 
@@ -68,7 +70,8 @@ struct PlanDev {
     int32_t nq, K, chunk, sigma;
     int32_t nbw, pq, band_cap, score_width;
     int32_t grid, prune;  // persistent CTAs of the join; bound pruning on/off
-    int32_t order, pad2;  // near-row order: 0 natural, 1 by bound, 2 by learned score
+    int32_t order, label;  // near-row order: 0 natural, 1 by bound, 2 by learned score; label dump on/off
+    MlpDev mlp;            // order 2 weights
     int64_t nhist;        // nq * 256 order buckets
     int64_t item_cap;     // capacity of item_ub
     int64_t X;     // slots = totA + totC
@@ -96,6 +99,7 @@ struct PlanDev {
     uint32_t* degv3;    // scan degree in ordered position
     int64_t* scan4;     // prefix of degv3
     float* mlp_pred;    // learned order key (order 2)
+    uint32_t* ubest;    // label dump: key of the best fp32 path through a near entry (ordered position)
     uint32_t* qkey;     // [2 nq] min / max order key per query
     uint32_t* hist;     // [nq * 256] bucket counts
     int64_t* hscan;     // [nq * 256 + 1]
