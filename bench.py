@@ -58,8 +58,10 @@ WORKLOAD_DESCS = {
 WORKLOAD_DESC = WORKLOAD_DESCS[WORKLOAD]
 DATA = "synthetic: seeded R-MAT typed knowledge graph standing in for WikiKG90Mv2"
 FORM_DESC = {"plain": "plain: batched, every middle edge scored, fp32 screen + fp64 rescoring",
-             "chosen": "chosen: plain + rows ordered by their score bound, a seed pass per query, provable "
-                       "bound pruning of work items, rows and hits (identical output)"}
+             "bound": "bound: plain + rows ordered by their score bound, a seed pass per query, provable "
+                      "bound pruning of work items, rows and hits (identical output)",
+             "chosen": "chosen: as bound, with rows ordered by the learned MLP score (trained on plain runs "
+                       "over 20,000 held-out queries before timing) (identical output)"}
 # kernels per step: k_init, k_expand, scan x3, k_lists, scan x3, k_plan, k_order_key,
 # k_order_hist, scan x3, k_order_perm, scan x3, k_near, k_middle (seed), k_middle,
 # k_merge1, k_rescore, k_merge2, k_exact
@@ -239,8 +241,22 @@ def run_gpu(args):
     n_out = torch.empty(nq, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
+    model, train_rep, train_s = None, None, 0.0
+    if args.form == "chosen" or args.all_forms:
+        t0 = time.perf_counter()
+        import synth
+        St, Tt = synth.queries_edge_biased(g, args.train_queries, seed=rank, stream=3)
+        model, train_rep = mhr.train_ordering_mlp(G, St, Tt, epochs=3, batch=4096, lr=2e-3)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+
     def make_opts(form):
-        o = {"prune": 0, "order": 0} if form == "plain" else {"prune": 1, "order": 1}
+        if form == "plain":
+            o = {"prune": 0, "order": 0}
+        elif form == "bound":
+            o = {"prune": 1, "order": 1}
+        else:
+            o = {"prune": 1, "order": 2, "mlp": model}
         if args.chunk:
             o["chunk"] = args.chunk
         return o
@@ -284,12 +300,17 @@ def run_gpu(args):
     elapsed_ms, join_ms, dev_ms, stats, clk = timed(opts, args.steps, clocks)
     wall1 = time.perf_counter()
     value = nq * ws * args.steps / (elapsed_ms / 1000.0)
-    other_form = "plain" if args.form == "chosen" else "chosen"
-    o_ms, o_join, o_dev, o_stats, _ = timed(make_opts(other_form), max(3, args.steps // 4))
-    o_steps = max(3, args.steps // 4)
-    other = {"form": FORM_DESC[other_form], "value": nq * ws * o_steps / (o_ms / 1000.0),
-             "ms_per_step": o_ms / o_steps, "join_ms": statistics.mean(o_join),
-             "work_per_step": {k: o_stats[k] for k in ("edges_scanned", "hits", "paths", "pruned_edges")}}
+    others = {}
+    for of in (["plain", "bound", "chosen"] if args.all_forms else ["plain"]):
+        if of == args.form:
+            continue
+        o_steps = max(3, args.steps // 4)
+        o_ms, o_join, o_dev, o_stats, _ = timed(make_opts(of), o_steps)
+        others[of] = {"form": FORM_DESC[of], "value": nq * ws * o_steps / (o_ms / 1000.0),
+                      "ms_per_step": o_ms / o_steps, "join_ms": statistics.mean(o_join),
+                      "work_per_step": {k: o_stats[k] for k in ("edges_scanned", "hits", "paths", "pruned_edges")}}
+        if of == "plain":
+            o_stats_plain = o_stats
 
     # end to end through the C ABI with host buffers (queries in, paths out)
     e2e_times = []
@@ -315,7 +336,7 @@ def run_gpu(args):
         s_near = sum(min(f["s_f"], f["s_b"]) for f in fs)
         n_vert = sum(f["n_u"] + f["n_v"] for f in fs)
         eb = 4 if g.dtype == "f32" else 2
-        plain_stats = stats if args.form == "plain" else o_stats
+        plain_stats = stats if args.form == "plain" else o_stats_plain
         # algorithmic bytes of one middle-join launch (the plain method): 4 B per
         # scanned CSR entry, 2 B relation id per hit, one embedding row per
         # distinct frontier vertex
@@ -351,7 +372,10 @@ def run_gpu(args):
                               "pruned_edges": stats["pruned_edges"],
                               "candidates": stats["candidates"], "rescored": stats["rescored"],
                               "dense_queries": stats["dense_queries"]},
-            "other_form": other,
+            "other_forms": others,
+            "learned_order": ({"train_queries": args.train_queries, "rows": train_rep.rows,
+                               "loss_first": train_rep.loss_first, "loss_last": train_rep.loss_last,
+                               "train_s": train_s} if train_rep else None),
             "device_ms_per_step": statistics.mean(dev_ms),
             "device_host_agree": agree,
             "wall_s_timed_loop": wall1 - wall0,
@@ -375,7 +399,9 @@ def main():
     ap.add_argument("--chunk", type=int, default=0, help="middle-join work item size (0 = default)")
     ap.add_argument("--workload", default="medium", choices=sorted(WORKLOAD_DESCS),
                     help="medium is the benchmark workload; the others are extra measurements")
-    ap.add_argument("--form", default="chosen", choices=["plain", "chosen"],
+    ap.add_argument("--all-forms", type=int, default=1, help="also time the other forms (plain, bound, chosen)")
+    ap.add_argument("--train-queries", type=int, default=20000)
+    ap.add_argument("--form", default="chosen", choices=["plain", "bound", "chosen"],
                     help="plain: every hit scored; chosen: provable bound pruning (same output)")
     args = ap.parse_args()
     global WORKLOAD, WORKLOAD_DESC
