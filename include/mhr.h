@@ -194,8 +194,11 @@ mhr_status mhr_topk_paths_batched(const mhr_graph* g, int32_t nq, const uint32_t
  * (s, t: host arrays) and writes, for every intermediate vertex x scanned by
  * the join that lies on at least one path, one training row: near_v[i] = x,
  * end_v[i] = the query endpoint on the far side of x (t when x is a hop-1
- * vertex, s when it is a hop-3 vertex), own[i] = the best fp32 weight of x's
- * own hop edge, best[i] = the best fp32 path score through x.  At most cap
+ * vertex, s when it is a hop-3 vertex), own[i] = the provable upper bound of
+ * the fp32 score of any path through x (the row bound the search prunes
+ * with), best[i] = the best fp32 path score through x (<= own[i]).  With
+ * order 2 a query orders rows by own + min(0, MLP(x, endpoint)), so the
+ * network learns the slack best - own.  At most cap
  * rows; *n_written (host) = rows written, or the number needed when > cap
  * (then MHR_ERANGE).  Synchronous.
  */

@@ -283,13 +283,14 @@ __global__ void k_lists(const PlanDev* __restrict__ P, DevGraph g) {
 // single block: direction choice and the work-item queue layout
 __global__ void __launch_bounds__(1024) k_plan(const PlanDev* __restrict__ P) {
     __shared__ int64_t sm[33];
+    __shared__ int64_t sm2[33];
     const int nq = P->nq;
     const int64_t totA = P->totA;
     const int64_t chunk = P->chunk;
-    int64_t carry = 0;
+    int64_t carry = 0, carry2 = 0;
     for (int base = 0; base < nq; base += blockDim.x) {
         const int q = base + threadIdx.x;
-        int64_t items = 0;
+        int64_t items = 0, nn = 0;
         if (q < nq) {
             const int64_t a0 = P->a_off[q], a1 = P->a_off[q + 1];
             const int64_t c0 = totA + P->c_off[q], c1 = totA + P->c_off[q + 1];
@@ -305,13 +306,22 @@ __global__ void __launch_bounds__(1024) k_plan(const PlanDev* __restrict__ P) {
             P->far_cnt[q] = static_cast<int32_t>(far_cnt);
             P->s_near[q] = s_near;
             items = (s_near + chunk - 1) / chunk;
+            nn = near_cnt;
         }
-        int64_t tot;
+        int64_t tot, tot2;
         const int64_t ex = block_excl_scan(items, sm, &tot);
-        if (q < nq) P->item_off[q] = carry + ex;
+        const int64_t ex2 = block_excl_scan(nn, sm2, &tot2);
+        if (q < nq) {
+            P->item_off[q] = carry + ex;
+            P->near_off[q] = carry2 + ex2;
+        }
         carry += tot;
+        carry2 += tot2;
     }
-    if (threadIdx.x == 0) P->item_off[nq] = carry;
+    if (threadIdx.x == 0) {
+        P->item_off[nq] = carry;
+        P->near_off[nq] = carry2;
+    }
 }
 
 // Position of slot x: side, query, region base.  Returns false for slots
@@ -336,29 +346,40 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_keys(const PlanDev* __restr
     __shared__ float part[kMlpRows][4];
     __shared__ uint32_t va[kMlpRows], vb[kMlpRows];
     __shared__ float own[kMlpRows];
-    __shared__ int ok[kMlpRows];
-    const int64_t X = P->X;
-    for (int64_t t0 = static_cast<int64_t>(blockIdx.x) * kMlpRows; t0 < X; t0 += static_cast<int64_t>(gridDim.x) * kMlpRows) {
+    __shared__ int64_t slot[kMlpRows];
+    __shared__ int qrow[kMlpRows];
+    const int nq = P->nq;
+    const int64_t rows = P->near_off[nq];
+    for (int64_t t0 = static_cast<int64_t>(blockIdx.x) * kMlpRows; t0 < rows; t0 += static_cast<int64_t>(gridDim.x) * kMlpRows) {
         if (threadIdx.x < kMlpRows) {
-            const int64_t x = t0 + threadIdx.x;
-            int q = 0;
-            int64_t base = 0;
-            bool sideA = true;
-            const bool v = x < X && near_slot(P, x, q, base, sideA);
-            ok[threadIdx.x] = v;
+            const int64_t r = t0 + threadIdx.x;
+            slot[threadIdx.x] = -1;
             va[threadIdx.x] = vb[threadIdx.x] = 0u;
             own[threadIdx.x] = 0.f;
-            if (v) {
+            if (r < rows) {
+                const int q = static_cast<int>(upper_bound_i64(P->near_off, nq + 1, r) - 1);
+                const bool fwd = P->dir[q] == 1;
+                const int64_t base = fwd ? P->a_off[q] : P->totA + P->c_off[q];
+                const int64_t x = base + (r - P->near_off[q]);
                 const ListEnt e = P->list[x];
+                slot[threadIdx.x] = x;
                 va[threadIdx.x] = e.vertex;
-                vb[threadIdx.x] = sideA ? P->T[q] : P->S[q];
-                own[threadIdx.x] = e.maxw;
+                vb[threadIdx.x] = fwd ? P->T[q] : P->S[q];
+                own[threadIdx.x] = P->bnat[x];
+                qrow[threadIdx.x] = q;
             }
         }
         __syncthreads();
-        auto a_pair = [&](int r, int k) -> uint32_t { return ok[r] ? feature_pair(g, va[r], vb[r], k) : 0u; };
+        auto a_pair = [&](int r, int k) -> uint32_t { return slot[r] >= 0 ? feature_pair(g, va[r], vb[r], k) : 0u; };
         auto store_y = [&](int r, float y) {
-            if (ok[r]) P->mlp_pred[t0 + r] = own[r] + y;
+            if (slot[r] >= 0) {
+                // order key: the row bound plus the predicted (non-positive) slack
+                const uint32_t key = f2key(__fadd_rn(own[r], fminf(y, 0.f)));
+                P->mlp_pred[slot[r]] = key2f(key);
+                P->okey[slot[r]] = key;
+                atomicMin(&P->qkey[2 * qrow[r]], key);
+                atomicMax(&P->qkey[2 * qrow[r] + 1], key);
+            }
         };
         auto store_z = [&](int, int, float) {};
         mlp_tile(P->mlp, a_pair, store_y, store_z, false, part);
@@ -385,8 +406,8 @@ __global__ void k_order_key(const PlanDev* __restrict__ P, DevGraph g) {
         if (sideA) b = __fadd_rn(__fadd_rn(e.maxw, g.maxw_out[e.vertex]), key2f(P->qmax[2 * q + 1]));
         else b = __fadd_rn(__fadd_rn(key2f(P->qmax[2 * q]), g.maxw_in[e.vertex]), e.maxw);
         P->bnat[x] = b;
-        if (order == 0) continue;
-        const uint32_t key = f2key(order == 1 ? b : P->mlp_pred[x]);
+        if (order != 1) continue;  // order 2 keys: k_mlp_keys
+        const uint32_t key = f2key(b);
         P->okey[x] = key;
         atomicMin(&P->qkey[2 * q], key);
         atomicMax(&P->qkey[2 * q + 1], key);
@@ -1482,12 +1503,13 @@ __global__ void k_dump_labels(const PlanDev* __restrict__ P, int64_t cap, uint32
         if (!near_slot(P, x, q, base, sideA)) continue;
         const uint32_t k = P->ubest[x];
         if (k == 0u) continue;
-        const ListEnt e = P->list[base + P->nperm[x]];
+        const int64_t nat = base + P->nperm[x];
+        const ListEnt e = P->list[nat];
         const unsigned long long i = atomicAdd(count, 1ull);
         if (static_cast<int64_t>(i) < cap) {
             near_v[i] = e.vertex;
             end_v[i] = sideA ? P->T[q] : P->S[q];
-            own[i] = e.maxw;
+            own[i] = P->bnat[nat];  // the row's provable score bound
             best[i] = key2f(k);
         }
     }
@@ -1671,8 +1693,8 @@ static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int
         e = device_excl_scan<uint32_t>(p->h.degv, nX, p->h.partials, p->h.scan2, st);
         if (e != cudaSuccess) return e;
         k_plan<<<1, 1024, 0, st>>>(d);
-        k_mlp_keys<<<sms * 8, kMlpThreads, 0, st>>>(d, g);
         k_order_key<<<sms * 4, 256, 0, st>>>(d, g);
+        k_mlp_keys<<<sms * 8, kMlpThreads, 0, st>>>(d, g);
         k_order_hist<<<sms * 4, 256, 0, st>>>(d);
         const int64_t* nH = reinterpret_cast<const int64_t*>(p->dregion + offsetof(PlanDev, nhist));
         e = device_excl_scan<uint32_t>(p->h.hist, nH, p->h.partials, p->h.hscan, st);
@@ -1766,6 +1788,7 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) 
     if ((rc = plan_alloc(p, &h.far_cnt, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.s_near, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.item_off, nq + 1)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.near_off, nq + 1)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.thr_g, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.qmax, 2 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.qkey, 2 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);

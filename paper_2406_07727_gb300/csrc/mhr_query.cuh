@@ -111,6 +111,7 @@ struct PlanDev {
     int32_t* far_cnt;
     int64_t* s_near;
     int64_t* item_off;
+    int64_t* near_off;  // [nq+1] prefix of near_cnt (rows of the learned-order MLP)
     uint32_t* thr_g;    // order-preserving key of the best known K-th fp32 score
     uint32_t* qmax;     // [2 nq] keys: max hop-1 weight, max hop-3 weight
     int32_t* dense;

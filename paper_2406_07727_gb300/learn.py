@@ -1,12 +1,13 @@
 """Learned ordering of intermediate vertices (training driver).
 
 The network is the library's ordering MLP (256 bfloat16 features [e_x[0:128];
-e_endpoint[0:128]] -> 256 ReLU units -> 1).  It is trained to predict the best
-completion of a path through an intermediate vertex x: the best fp32 path
-score through x minus x's own best hop weight, both produced by plain (exact,
-unpruned) runs of the search (``mhr_training_labels``).  At query time the
-library orders the rows it scans by own weight + prediction so the K-th score
-of a query rises early; pruning stays bound-based, so results never change.
+e_endpoint[0:128]] -> 256 ReLU units -> 1).  It is trained to predict the
+slack of the search's provable row bound for an intermediate vertex x: the
+best fp32 path score through x minus that bound, both produced by plain
+(exact, unpruned) runs of the search (``mhr_training_labels``).  At query
+time the library orders the rows it scans by bound + min(0, prediction), so
+the K-th score of a query rises early; pruning stays bound-based, so results
+never change.
 
 This module only drives: data movement, shuffling and the epoch loop run on
 the host; labels, features, forward, backward and Adam run in the library's
@@ -81,7 +82,7 @@ class TrainReport:
 
 
 def collect_labels(G, S, T, queries_per_call: int = 256, cap: int = 1 << 22):
-    """Training rows from plain runs: (near_v, end_v, completion target) on the host."""
+    """Training rows from plain runs: (near_v, end_v, slack target) on the host."""
     nv, ev, tg = [], [], []
     for i in range(0, len(S), queries_per_call):
         s, t = S[i:i + queries_per_call], T[i:i + queries_per_call]
@@ -97,7 +98,7 @@ def collect_labels(G, S, T, queries_per_call: int = 256, cap: int = 1 << 22):
             a, b, own, best = _mhr.mhr_training_labels(G, s, t, cap * 8)
         nv.append(a.cpu().numpy().view(np.uint32))
         ev.append(b.cpu().numpy().view(np.uint32))
-        tg.append((best - own).cpu().numpy())
+        tg.append(best.cpu().numpy() - own.cpu().numpy())
     return np.concatenate(nv), np.concatenate(ev), np.concatenate(tg).astype(np.float32)
 
 

@@ -124,6 +124,8 @@ def test_training_labels_match_path_enumeration(mhr):
     near_v = near_v.cpu().numpy().view(np.uint32)
     end_v = end_v.cpu().numpy().view(np.uint32)
     best = best.cpu().numpy()
+    # the row bound the search prunes with is an upper bound of every path through the row
+    assert np.all(best <= own.cpu().numpy())
     m = MITM(g, "transe")
     exact = {}
     for s, t in zip(S.tolist(), T.tolist()):
