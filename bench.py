@@ -54,6 +54,8 @@ WORKLOAD_DESCS = {
                  "per step with log-uniform source degree in [1,1e5], K=50, TransE-L1 (gamma=1)"),
     "tiny": ("Zipf(2.1) typed KG: 10,000 vertices, 100,000 edges, 8 relations, d=64 fp32 ~N(0,1/8); "
              "one hub query, K=10, TransE-L1"),
+    "precision": ("the medium R-MAT graph (1,000,000 vertices, 20,000,000 edges, 16 relations) with d=256 "
+                  "fp32 embeddings ~N(0,1/sqrt(d)); 256 edge-biased queries per step, K=100, DistMult"),
 }
 WORKLOAD_DESC = WORKLOAD_DESCS[WORKLOAD]
 DATA = "synthetic: seeded R-MAT typed knowledge graph standing in for WikiKG90Mv2"
@@ -233,7 +235,9 @@ def run_gpu(args):
 
     g, S, T, K, spec = load_workload(rank)
     nq = len(S)
-    G = mhr.load_kg(g, score_fn="transe")
+    score_fn = spec.get("score", "transe")
+    G = mhr.load_kg(g, score_fn=score_fn)
+    tc = 1 if score_fn == "distmult" else 0   # tensor-core middle-edge screen for DistMult
     stream = torch.cuda.current_stream()
     dS = torch.from_numpy(S.astype(np.int32)).cuda()
     dT = torch.from_numpy(T.astype(np.int32)).cuda()
@@ -254,9 +258,9 @@ def run_gpu(args):
         if form == "plain":
             o = {"prune": 0, "order": 0}
         elif form == "bound":
-            o = {"prune": 1, "order": 1}
+            o = {"prune": 1, "order": 1, "precision": tc}
         else:
-            o = {"prune": 1, "order": 2, "mlp": model}
+            o = {"prune": 1, "order": 2, "mlp": model, "precision": tc}
         if args.chunk:
             o["chunk"] = args.chunk
         return o
@@ -352,7 +356,8 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": DATA,
             "config": {"workload": WORKLOAD_DESC, "queries_per_step": nq, "K": K,
-                       "score_fn": "transe_l1", "form": FORM_DESC[args.form],
+                       "score_fn": score_fn, "form": FORM_DESC[args.form],
+                       "middle_edge_screen": "bf16 tensor cores (hi/lo split)" if (tc and args.form != "plain") else "fp32 CUDA cores",
                        "l2": "flushed before every step (256 MiB write, excluded from the step time)",
                        "parallelism": "replicas (each rank its own queries)" if ws > 1 else "single GPU",
                        "launch": "three CUDA graphs per step (before / join / after)"},

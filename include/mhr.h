@@ -121,7 +121,9 @@ typedef struct {
                             bound, 2 by the learned score of `mlp` */
     int32_t prune;       /* 1 = skip work items, rows and middle edges whose provable
                             score bound cannot reach the kept band (same result) */
-    int32_t reserved0;
+    int32_t precision;   /* middle-edge screen: 0 fp32 CUDA cores; 1 bf16 tensor-core
+                            contraction with hi/lo split and fp32 accumulation (DistMult,
+                            at most 16 relations); the fp64 rescoring keeps results exact */
     const mhr_mlp* mlp;  /* order == 2 only */
     int32_t reserved[2];
 } mhr_query_opts;

@@ -57,7 +57,7 @@ class MLP(ctypes.Structure):
 
 class QueryOpts(ctypes.Structure):
     _fields_ = [("chunk", ctypes.c_int32), ("order", ctypes.c_int32), ("prune", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("mlp", ctypes.POINTER(MLP)),
+                ("precision", ctypes.c_int32), ("mlp", ctypes.POINTER(MLP)),
                 ("reserved", ctypes.c_int32 * 2)]
 
 

@@ -14,6 +14,7 @@
 
 #include "mhr_internal.cuh"
 #include "mhr_util.cuh"
+#include <cuda_bf16.h>
 
 static_assert(sizeof(mhr_graph_desc) == 104, "mhr_graph_desc layout");
 static_assert(sizeof(mhr_path) == 24, "mhr_path layout");
@@ -218,6 +219,35 @@ static void compute_bounds(mhr_graph* g) {
     const double path = 3.0 * (eps32 + eps64) +
                         (gam(2, u32) + gam(2, u64)) * 3.0 * (wmax + eps32 + eps64);
     g->err_path = path * (1.0 + 1e-6) + 1e-300;
+    // Tensor-core middle-edge screen (DistMult): p_j = fl32(e_u[j] e_v[j]) is
+    // split p = p_hi + p_lo + r with bf16 parts, |r| <= 2^-16 |p|; w_r likewise;
+    // the products p_hi w_hi + p_hi w_lo + p_lo w_hi are exact in fp32 and the
+    // dropped p_lo w_lo is <= 2^-16 |p w|, so each term is within
+    // (2^-24 + 4 * 2^-16) |e_u e_v w| of the exact one.  The tensor-core fp32
+    // accumulation (3 products per term, order unspecified) is bounded with a
+    // unit roundoff of 2^-22 to allow for its alignment truncation.
+    if (g->fn == MHR_SCORE_DISTMULT) {
+        const double M = g->max_rel_inf * g->max_l2sq;
+        const double term = std::ldexp(1.0, -24) + 4.0 * std::ldexp(1.0, -16);
+        const double epstc = (term + gam(3.0 * d + 3, std::ldexp(1.0, -22)) * (1.0 + term)) * M;
+        g->epstc_edge = epstc;
+        const double ptc = 2.0 * eps32 + epstc + 3.0 * eps64 +
+                           (gam(2, u32) + gam(2, u64)) * 3.0 * (wmax + epstc + eps32 + eps64);
+        g->err_path_tc = ptc * (1.0 + 1e-6) + 1e-300;
+    }
+}
+
+// bf16 hi / lo split of the relation table (tensor-core middle-edge screen)
+__global__ void k_split_rel(const void* __restrict__ remb, int dtype, int64_t count, uint16_t* __restrict__ hi,
+                            uint16_t* __restrict__ lo) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count; i += stride) {
+        const float w = dtype == MHR_F32 ? static_cast<const float*>(remb)[i]
+                                         : bf16_to_f32(static_cast<const uint16_t*>(remb)[i]);
+        const __nv_bfloat16 h = __float2bfloat16_rn(w);
+        hi[i] = __bfloat16_as_ushort(h);
+        lo[i] = __bfloat16_as_ushort(__float2bfloat16_rn(w - __bfloat162float(h)));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -479,6 +509,13 @@ mhr_status load_impl(const mhr_graph_desc* desc, mhr_graph* g, cudaStream_t st) 
     dg.remb = remb;
     g->fn = desc->score_fn;
     compute_bounds(g);
+    if (g->fn == MHR_SCORE_DISTMULT) {
+        const int64_t cnt = static_cast<int64_t>(R) * d;
+        MHR_TRY(graph_alloc(g, reinterpret_cast<void**>(&g->wsplit), sizeof(uint16_t) * 2 * cnt));
+        k_split_rel<<<std::max(1, std::min(grid, static_cast<int>((cnt + 255) / 256))), 256, 0, st>>>(
+            remb, desc->emb_dtype, cnt, g->wsplit, g->wsplit + cnt);
+        MHR_CUDA_TRY(cudaGetLastError());
+    }
     // per-vertex bounds on the fp32 weight of adjacent edges (bound pruning)
     {
         uint32_t *kout, *kin;

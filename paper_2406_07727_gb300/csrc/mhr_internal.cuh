@@ -77,6 +77,10 @@ struct mhr_graph {
     int64_t max_out_deg = 0, max_in_deg = 0;
     // fp32 screening error bounds (see mhr_graph.cu)
     double eps32_edge = 0, eps64_edge = 0, err_path = 0;
+    // tensor-core screen of the middle edge (DistMult, bf16 hi/lo split):
+    // per-edge bound and the path bound when w2 comes from it
+    double epstc_edge = 0, err_path_tc = 0;
+    uint16_t* wsplit = nullptr;  // [2][R][d] bf16 hi / lo parts of the relation table
     double max_l1 = 0, max_rel_l1 = 0, max_rel_inf = 0, max_l2sq = 0;
     int num_sms = 0;
     mhr::PlanCache* plans = nullptr;

@@ -703,10 +703,105 @@ __device__ __forceinline__ void item_edges(const PlanDev* __restrict__ P, int64_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core screen of the middle edges of a warp batch (DistMult, R <= 16).
+// For hit h (lane h) the weight of every relation is (e_u (*) e_v) . W^T: the
+// products p = fl32(e_u[j] e_v[j]) form a 32 x d bf16 hi/lo matrix, the
+// relation table a d x R one, and three m16n8k16 products (hi.hi, hi.lo,
+// lo.hi) accumulate in fp32.  Lane h returns the weight of its own relation.
+__device__ __forceinline__ float2 emb_pair(const DevGraph& g, uint32_t v, int k) {
+    float2 r = make_float2(0.f, 0.f);
+    if (k < g.d) r.x = emb_f32(g.vemb, g.dtype, v, g.d, k);
+    if (k + 1 < g.d) r.y = emb_f32(g.vemb, g.dtype, v, g.d, k + 1);
+    return r;
+}
+
+__device__ __forceinline__ void split_pair(float2 p, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat16 hx = __float2bfloat16_rn(p.x), hy = __float2bfloat16_rn(p.y);
+    const float rx = p.x - __bfloat162float(hx), ry = p.y - __bfloat162float(hy);
+    hi = static_cast<uint32_t>(__bfloat16_as_ushort(hx)) | (static_cast<uint32_t>(__bfloat16_as_ushort(hy)) << 16);
+    lo = pack_bf16x2(rx, ry);
+}
+
+__device__ float tc_batch_w2(const DevGraph& g, const uint16_t* __restrict__ wsplit, uint32_t hu, uint32_t hv,
+                             uint32_t hr2, int lane) {
+    const int gq = lane >> 2, tq = lane & 3;
+    const int R = g.R, d = g.d;
+    const int64_t rd = static_cast<int64_t>(R) * d;
+    float acc[2][2][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) acc[a][b][0] = acc[a][b][1] = acc[a][b][2] = acc[a][b][3] = 0.f;
+    uint32_t ru[2][2], rv[2][2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int hlf = 0; hlf < 2; ++hlf) {
+            ru[mt][hlf] = __shfl_sync(0xffffffffu, hu, mt * 16 + gq + 8 * hlf);
+            rv[mt][hlf] = __shfl_sync(0xffffffffu, hv, mt * 16 + gq + 8 * hlf);
+        }
+    for (int kt = 0; kt < (d + 15) / 16; ++kt) {
+        const int k = kt * 16 + tq * 2;
+        uint32_t bh[2][2], bl[2][2];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int n = nt * 8 + gq;
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+                const int kc = k + 8 * kk;
+                uint32_t h = 0u, l = 0u;
+                if (n < R) {
+                    const int64_t i = static_cast<int64_t>(n) * d + kc;
+                    const uint32_t h0 = kc < d ? wsplit[i] : 0u, h1 = kc + 1 < d ? wsplit[i + 1] : 0u;
+                    const uint32_t l0 = kc < d ? wsplit[rd + i] : 0u, l1 = kc + 1 < d ? wsplit[rd + i + 1] : 0u;
+                    h = h0 | (h1 << 16);
+                    l = l0 | (l1 << 16);
+                }
+                bh[nt][kk] = h;
+                bl[nt][kk] = l;
+            }
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            uint32_t ah[4], al[4];
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) {
+                // q4: 0 -> (row g, k), 1 -> (row g+8, k), 2 -> (row g, k+8), 3 -> (row g+8, k+8)
+                const int hlf = q4 & 1, kc = k + 8 * (q4 >> 1);
+                const float2 a = emb_pair(g, ru[mt][hlf], kc), b = emb_pair(g, rv[mt][hlf], kc);
+                split_pair(make_float2(a.x * b.x, a.y * b.y), ah[q4], al[q4]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                mma_bf16_16816(acc[mt][nt], ah[0], ah[1], ah[2], ah[3], bh[nt][0], bh[nt][1]);
+                mma_bf16_16816(acc[mt][nt], ah[0], ah[1], ah[2], ah[3], bl[nt][0], bl[nt][1]);
+                mma_bf16_16816(acc[mt][nt], al[0], al[1], al[2], al[3], bh[nt][0], bh[nt][1]);
+            }
+        }
+    }
+    // lane h wants row h, column r2: held by lane ((h % 16) % 8) * 4 + (r2 % 8) / 2,
+    // register [h / 16][r2 / 8][((h % 16) / 8) * 2 + r2 % 2]
+    const int h = lane;
+    const int src = ((h & 15) & 7) * 4 + (static_cast<int>(hr2 & 7) >> 1);
+    const int want = (h >> 4) * 8 + (static_cast<int>(hr2 >> 3) & 1) * 4 + ((h & 15) >> 3) * 2 + static_cast<int>(hr2 & 1);
+    float w = 0.f;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float v = __shfl_sync(0xffffffffu, acc[mt][nt][j], src);
+                if (want == mt * 8 + nt * 4 + j) w = v;
+            }
+    return w;
+}
+
 // SEED: with bound pruning on, a first launch processes only the first work
 // item of every query (its highest-bound rows when rows are ordered), so the
 // shared K-th score of every query is set before the main launch starts.
-template <int UNROLL, bool SEED>
+template <int UNROLL, bool SEED, bool TC>
 __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __restrict__ P, DevGraph g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MidSmem& sm = *reinterpret_cast<MidSmem*>(smem_raw);
@@ -719,6 +814,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
     Hit* hits = P->hits + static_cast<int64_t>(blockIdx.x) * kMaxChunk;
     unsigned long long n_scanned = 0, n_hits = 0, n_cands = 0, n_paths_w = 0, n_pruned = 0, n_skipped = 0;
     const bool prune = P->prune != 0;
+    const float slack = P->prune_slack;
     if (SEED && !prune) return;
 #ifdef MHR_PHASE_TIMING
     // cycles per phase, thread 0: 0 fetch + query switch, 1 item setup, 2 scan, 3 score
@@ -801,7 +897,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                     else {
                         uint32_t gk = atomicOr(&P->thr_g[iq], 0u);
                         if (iq == sm.q && sm.lt_key > gk) gk = sm.lt_key;
-                        if (gk != 0u && key2f(P->item_ub[it]) < keep_threshold(gk, two_err)) {
+                        if (gk != 0u && __fadd_ru(key2f(P->item_ub[it]), P->prune_slack) < keep_threshold(gk, two_err)) {
                             skip = true;
                             ++n_skipped;
                         }
@@ -941,7 +1037,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                     valid[u] = e < e1;
                     if (prune) {
                         // no path through this row can reach the kept band: skip its edges
-                        const float rowb = __shfl_sync(FULL, rb[u], c);
+                        const float rowb = __fadd_ru(__shfl_sync(FULL, rb[u], c), slack);
                         if (valid[u] && rowb < thr_scan) {
                             valid[u] = false;
                             ++n_pruned;
@@ -1066,7 +1162,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                             if (prune) {
                                 // w2 <= max weight of the scanned vertex's adjacent edges
                                 const float mw2 = sm.dir ? g.maxw_out[hu] : g.maxw_in[hv];
-                                if (__fadd_rn(__fadd_rn(mw1, mw2), mw3) < thr) {
+                                if (__fadd_ru(__fadd_rn(__fadd_rn(mw1, mw2), mw3), slack) < thr) {
                                     alive = false;
                                     ++n_pruned;
                                 }
@@ -1093,6 +1189,9 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                         const bool live2 = prune ? (lane < nsurv) : live;
                         const int rounds = prune ? (nsurv + H - 1) / H : G;
                         float w2m = 0.f;
+                        if (TC) {
+                            w2m = tc_batch_w2(g, P->wsplit, hu, hv, hr2, lane);
+                        } else
                         for (int r = 0; r < rounds; ++r) {
                             const int src = r * H + lane / G;
                             const uint32_t u = __shfl_sync(FULL, hu, src);
@@ -1519,7 +1618,7 @@ __global__ void k_dump_labels(const PlanDev* __restrict__ P, int64_t cap, uint32
 // host side: plans (buffers + captured graph) per (nq, K, chunk)
 // ===========================================================================
 struct Plan {
-    int nq = 0, K = 0, chunk = 0, grid = 0;
+    int nq = 0, K = 0, chunk = 0, grid = 0, precision = 0;
     PlanDev h{};
     unsigned char* dregion = nullptr;  // [PlanDev][S][T][a_off][c_off]
     size_t region_bytes = 0;
@@ -1555,7 +1654,7 @@ struct Plan {
 };
 
 struct PlanCache {
-    std::map<std::tuple<int, int, int>, Plan*> plans;
+    std::map<std::tuple<int, int, int, int>, Plan*> plans;
     ~PlanCache() {
         for (auto& kv : plans) delete kv.second;
     }
@@ -1704,8 +1803,13 @@ static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int
         if (e != cudaSuccess) return e;
         k_near<<<sms * 4, 256, 0, st>>>(d, g);
     } else if (part == 1) {
-        k_middle<kUnroll, true><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
-        k_middle<kUnroll, false><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
+        if (p->precision) {
+            k_middle<kUnroll, true, true><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
+            k_middle<kUnroll, false, true><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
+        } else {
+            k_middle<kUnroll, true, false><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
+            k_middle<kUnroll, false, false><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
+        }
     } else {
         k_merge1<<<std::min(p->nq, sms * 2), 1024, 0, st>>>(d);
         k_rescore<<<sms * 4, kRsWarps * 32, 0, st>>>(d, g);
@@ -1755,17 +1859,24 @@ static int hit_group_width(int d, int dtype) {
     return w;
 }
 
+static float __double2float_ru_host(double x) {
+    float f = static_cast<float>(x);
+    if (static_cast<double>(f) < x) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
 static int choose_sigma(int64_t n) {
     int sigma = 0;
     while (((n - 1) >> sigma) >= static_cast<int64_t>(kMaxBmWords) * 32) ++sigma;
     return sigma;
 }
 
-static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) {
+static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precision, Plan** out) {
     Plan* p = new Plan();
     p->nq = nq;
     p->K = K;
     p->chunk = chunk;
+    p->precision = precision;
     p->grid = std::max(1, G->num_sms);
     PlanDev& h = p->h;
     h.nq = nq;
@@ -1775,7 +1886,10 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) 
     h.nbw = static_cast<int32_t>(((G->dg.n - 1) >> h.sigma) / 32 + 1);
     h.pq = 8 * K + 2048;
     h.band_cap = K + 2048;
-    h.err_path = G->err_path;
+    h.err_path = precision ? G->err_path_tc : G->err_path;
+    h.precision = precision;
+    h.prune_slack = precision ? __double2float_ru_host((G->epstc_edge + G->eps32_edge) * 1.01) : 0.f;
+    h.wsplit = G->wsplit;
     h.score_width = hit_group_width(G->dg.d, G->dg.dtype);
     mhr_status rc = MHR_OK;
     auto bail = [&](mhr_status r) {
@@ -1826,11 +1940,14 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) 
         e = cudaEventCreate(&ev);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
     }
-    e = cudaFuncSetAttribute(k_middle<kUnroll, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(mid_smem_bytes()));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_middle<kUnroll, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(mid_smem_bytes()));
+    {
+        const int sb = static_cast<int>(mid_smem_bytes());
+        const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        e = cudaFuncSetAttribute(k_middle<kUnroll, true, false>, a, sb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_middle<kUnroll, false, false>, a, sb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_middle<kUnroll, true, true>, a, sb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_middle<kUnroll, false, true>, a, sb);
+    }
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaFuncSetAttribute (middle join)"));
     e = cudaFuncSetAttribute(k_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(exact_smem_bytes()));
@@ -1842,9 +1959,9 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) 
     return MHR_OK;
 }
 
-static mhr_status get_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) {
+static mhr_status get_plan(mhr_graph* G, int nq, int K, int chunk, int precision, Plan** out) {
     if (!G->plans) G->plans = new PlanCache();
-    auto key = std::make_tuple(nq, K, chunk);
+    auto key = std::make_tuple(nq, K, chunk, precision);
     auto it = G->plans->plans.find(key);
     if (it != G->plans->plans.end()) {
         *out = it->second;
@@ -1856,7 +1973,7 @@ static mhr_status get_plan(mhr_graph* G, int nq, int K, int chunk, Plan** out) {
         G->plans->plans.erase(G->plans->plans.begin());
     }
     Plan* p = nullptr;
-    MHR_TRY(make_plan(G, nq, K, chunk, &p));
+    MHR_TRY(make_plan(G, nq, K, chunk, precision, &p));
     G->plans->plans[key] = p;
     *out = p;
     return MHR_OK;
@@ -1867,8 +1984,13 @@ static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint
     int chunk = (opts && opts->chunk > 0) ? opts->chunk : kDefaultChunk;
     if (chunk > kMaxChunk || chunk < 32 || (chunk & 31))
         return fail(MHR_EINVAL, "opts->chunk must be a multiple of 32 in [32, 16384]");
+    const int precision = opts ? opts->precision : 0;
+    if (precision != 0 && precision != 1) return fail(MHR_EINVAL, "opts->precision must be 0 or 1");
+    if (precision == 1 && (G->fn != MHR_SCORE_DISTMULT || G->dg.R > 16 || !G->wsplit))
+        return fail(MHR_EINVAL, "the tensor-core screen (precision 1) needs DistMult and at most 16 relations");
+    if (precision == 1 && label) return fail(MHR_EINVAL, "label runs use the plain search");
     Plan* p = nullptr;
-    MHR_TRY(get_plan(G, nq, K, chunk, &p));
+    MHR_TRY(get_plan(G, nq, K, chunk, precision, &p));
     // sizes from the host copy of the row starts
     const RegionLayout L = region_layout(nq);
     if (p->h2d_pending) {

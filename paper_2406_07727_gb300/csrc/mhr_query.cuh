@@ -71,6 +71,9 @@ struct PlanDev {
     int32_t nbw, pq, band_cap, score_width;
     int32_t grid, prune;  // persistent CTAs of the join; bound pruning on/off
     int32_t order, label;  // near-row order: 0 natural, 1 by bound, 2 by learned score; label dump on/off
+    int32_t precision;     // 0 fp32 CUDA-core middle-edge screen, 1 bf16 tensor-core screen (DistMult)
+    float prune_slack;     // added to every pruning bound when the middle edge comes from the tensor cores
+    const uint16_t* wsplit;  // [2][R][d] bf16 hi / lo relation table
     MlpDev mlp;            // order 2 weights
     int64_t nhist;        // nq * 256 order buckets
     int64_t item_cap;     // capacity of item_ub

@@ -354,3 +354,40 @@ def test_batching_workload_sampled(mhr):
     want, n_want = oracle.topk_paths_batch(g, S[sample], T[sample], K)
     for i, q in enumerate(sample):
         compare_query(base_out[q], int(base_n[q]), want[i, : n_want[i]], ctx=int(q))
+
+
+@pytest.mark.parametrize("prune", [0, 1])
+def test_tensor_core_screen_distmult(mhr, prune):
+    """precision 1: middle edges screened by the bf16 hi/lo tensor-core
+    contraction; results identical to the oracle (and to precision 0)."""
+    rng = np.random.default_rng(41 + prune)
+    for trial in range(10):
+        n = int(rng.integers(20, 400))
+        d = int(rng.choice([3, 8, 16, 37, 64, 256]))
+        R = int(rng.integers(1, 17))
+        dtype = "bf16" if trial % 3 == 0 else "f32"
+        g = random_kg(rng, n, int(rng.integers(50, 25 * n)), R, d, dtype=dtype, dyadic=(trial % 4 == 0))
+        S = rng.integers(0, n, 16).astype(np.uint32)
+        T = rng.integers(0, n, 16).astype(np.uint32)
+        run_and_compare(mhr, g, S, T, int(rng.choice([1, 10, 100])), "distmult",
+                        opts={"precision": 1, "prune": prune, "order": prune})
+    g = synth.gen_rmat_kg(13, 6000, 120_000, 16, 3, seed=42)
+    g.vemb, g.remb = synth.gen_embeddings(g.n, g.R, 256, 1 / 16, seed=42)
+    S, T = synth.queries_edge_biased(g, 24, seed=42)
+    run_and_compare(mhr, g, S, T, 100, "distmult", opts={"precision": 1, "prune": prune, "order": prune})
+
+
+def test_tensor_core_screen_rejects_unsupported(mhr):
+    gj = load_golden()
+    g = kg_from_golden(gj)
+    G = mhr.load_kg(g, score_fn="transe")
+    with pytest.raises(mhr.MhrError) as e:
+        mhr.mhr_topk_paths(G, 0, 9, 5, opts={"precision": 1})
+    assert e.value.status == mhr.MHR_EINVAL
+    G.close()
+    rng = np.random.default_rng(5)
+    g = random_kg(rng, 50, 400, 20, 8)
+    G = mhr.load_kg(g, score_fn="distmult")
+    with pytest.raises(mhr.MhrError):
+        mhr.mhr_topk_paths(G, 0, 1, 5, opts={"precision": 1})
+    G.close()
