@@ -243,40 +243,51 @@ __global__ void k_lists(const PlanDev* __restrict__ P, DevGraph g) {
     const int64_t X = P->X, totA = P->totA;
     const int nq = P->nq;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < X; x += stride) {
-        if (!P->flag[x]) continue;
-        const bool sideA = x < totA;
-        const int64_t lx = sideA ? x : x - totA;
-        const int64_t* offs = sideA ? P->a_off : P->c_off;
-        const int q = static_cast<int>(upper_bound_i64(offs, nq + 1, lx) - 1);
-        const int64_t k = lx - offs[q];
-        const int64_t rlen = offs[q + 1] - offs[q];
-        const int64_t base = sideA ? offs[q] : totA + offs[q];
-        const int64_t j = P->scan1[x] - P->scan1[base];
-        const uint32_t s = P->S[q], t = P->T[q];
-        const uint32_t* cc = sideA ? g.col + g.off[s] : g.rcol + g.roff[t];
-        const uint32_t vtx = cc[k];
-        float mw = P->w32[x];
-        int64_t len = 1;
-        while (k + len < rlen && cc[k + len] == vtx) {
-            mw = fmaxf(mw, P->w32[x + len]);
-            ++len;
+    // uniform trip count so whole warps reach the per-query max reduction
+    const int64_t first = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    const int64_t iters = (X + stride - 1) / stride;
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t x = first + it * stride;
+        uint32_t qkey = 0xffffffffu, mkey = 0u;
+        if (x < X && P->flag[x]) {
+            const bool sideA = x < totA;
+            const int64_t lx = sideA ? x : x - totA;
+            const int64_t* offs = sideA ? P->a_off : P->c_off;
+            const int q = static_cast<int>(upper_bound_i64(offs, nq + 1, lx) - 1);
+            const int64_t k = lx - offs[q];
+            const int64_t rlen = offs[q + 1] - offs[q];
+            const int64_t base = sideA ? offs[q] : totA + offs[q];
+            const int64_t j = P->scan1[x] - P->scan1[base];
+            const uint32_t s = P->S[q], t = P->T[q];
+            const uint32_t* cc = sideA ? g.col + g.off[s] : g.rcol + g.roff[t];
+            const uint32_t vtx = cc[k];
+            float mw = P->w32[x];
+            int64_t len = 1;
+            while (k + len < rlen && cc[k + len] == vtx) {
+                mw = fmaxf(mw, P->w32[x + len]);
+                ++len;
+            }
+            ListEnt e;
+            e.vertex = vtx;
+            e.run_start = static_cast<uint32_t>(k);
+            e.run_len = static_cast<uint32_t>(len);
+            e.maxw = mw;
+            if (sideA) {
+                e.deg = static_cast<uint32_t>(g.off[vtx + 1] - g.off[vtx]);
+                e.rowstart = static_cast<uint32_t>(g.off[vtx]);
+            } else {
+                e.deg = static_cast<uint32_t>(g.roff[vtx + 1] - g.roff[vtx]);
+                e.rowstart = static_cast<uint32_t>(g.roff[vtx]);
+            }
+            P->list[base + j] = e;
+            P->degv[base + j] = e.deg;
+            qkey = 2u * static_cast<uint32_t>(q) + (sideA ? 0u : 1u);
+            mkey = f2key(mw);
         }
-        ListEnt e;
-        e.vertex = vtx;
-        e.run_start = static_cast<uint32_t>(k);
-        e.run_len = static_cast<uint32_t>(len);
-        e.maxw = mw;
-        if (sideA) {
-            e.deg = static_cast<uint32_t>(g.off[vtx + 1] - g.off[vtx]);
-            e.rowstart = static_cast<uint32_t>(g.off[vtx]);
-        } else {
-            e.deg = static_cast<uint32_t>(g.roff[vtx + 1] - g.roff[vtx]);
-            e.rowstart = static_cast<uint32_t>(g.roff[vtx]);
-        }
-        P->list[base + j] = e;
-        P->degv[base + j] = e.deg;
-        atomicMax(&P->qmax[2 * q + (sideA ? 0 : 1)], f2key(mw));
+        // per-(query, side) maximum: one atomic per group of lanes with the same key
+        const unsigned peers = __match_any_sync(0xffffffffu, qkey);
+        const uint32_t m = __reduce_max_sync(peers, mkey);
+        if (qkey != 0xffffffffu && (threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(&P->qmax[qkey], m);
     }
 }
 
@@ -486,6 +497,7 @@ __global__ void k_near(const PlanDev* __restrict__ P, DevGraph g) {
 // ===========================================================================
 constexpr int kRelCacheVecs = 512;  // 8 KB of fp32 relation embeddings
 constexpr int kSeedEdges = 2048;    // edges of each query's highest-bound rows done by the seed launch
+constexpr int kSeedMinItems = 2;    // queries with fewer work items are not seeded
 
 struct MidSmem {
     uint32_t bm[kMaxBmWords];
@@ -691,13 +703,22 @@ __device__ __forceinline__ float hit_w32_f32(const DevGraph& g, NearRow& nr, uin
 // edge range [e0, e1) of a work item in the query's near-edge space; the seed
 // launch does the first kSeedEdges edges of the first item, the main launch the
 // rest of it
+// A query is seeded (its first kSeedEdges edges done by the seed launch) when
+// pruning is on and it has at least kSeedMinItems work items.
+__device__ __forceinline__ bool seeded_query(const PlanDev* __restrict__ P, int q, bool prune) {
+    return prune && P->item_off[q + 1] - P->item_off[q] >= kSeedMinItems;
+}
+
+// edge range [e0, e1) of a work item in the query's near-edge space; for a
+// seeded query the seed launch does the first kSeedEdges edges of the first
+// item and the main launch the rest of it
 template <bool SEED>
 __device__ __forceinline__ void item_edges(const PlanDev* __restrict__ P, int64_t item, int q, bool prune,
                                            int64_t& e0, int64_t& e1) {
     const int64_t s_near = P->s_near[q];
     e0 = (item - P->item_off[q]) * P->chunk;
     e1 = min(e0 + static_cast<int64_t>(P->chunk), s_near);
-    if (prune && e0 == 0) {
+    if (e0 == 0 && seeded_query(P, q, prune)) {
         if (SEED) e1 = min(e1, static_cast<int64_t>(kSeedEdges));
         else e0 = min(e1, static_cast<int64_t>(kSeedEdges));
     }
@@ -857,7 +878,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                         for (;;) {
                             const int qq = static_cast<int>(atomicAdd(&P->counters[kCntSeed], 1ull));
                             if (qq >= nq) break;
-                            if (P->item_off[qq + 1] > P->item_off[qq]) {
+                            if (seeded_query(P, qq, prune)) {
                                 it = P->item_off[qq];
                                 break;
                             }
@@ -893,7 +914,9 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                 // row of the item can reach the query's kept band
                 bool skip = atomicOr(&P->dense[iq], 0) != 0;
                 if (!SEED && prune && !skip) {
-                    if (it == P->item_off[iq] && P->s_near[iq] <= kSeedEdges) skip = true;
+                    if (it == P->item_off[iq] && seeded_query(P, iq, prune) &&
+                        min(static_cast<int64_t>(P->chunk), P->s_near[iq]) <= kSeedEdges)
+                        skip = true;  // the seed launch did all of it
                     else {
                         uint32_t gk = atomicOr(&P->thr_g[iq], 0u);
                         if (iq == sm.q && sm.lt_key > gk) gk = sm.lt_key;
@@ -1343,13 +1366,15 @@ __global__ void __launch_bounds__(1024) k_merge1(const PlanDev* __restrict__ P) 
     }
 }
 
-// fp64 rescoring of the band, one warp per candidate.  The canonical order
-// fixes only the accumulation acc = acc + y_j (j ascending); the terms
-// y_j = |(a_j + b_j) - c_j| (or (a_j * b_j) * c_j) are independent, so lanes
-// compute them in parallel into shared memory and three lanes (one per edge)
-// then run the three sequential fp64 sums.
+// fp64 rescoring of the band.  The canonical order fixes only the
+// accumulation acc = acc + y_j (j ascending); the terms y_j = |(a_j + b_j) - c_j|
+// (or (a_j * b_j) * c_j) are independent.  A warp takes up to ten candidates
+// (thirty edge sums): all lanes compute terms into shared memory, then lane e
+// runs the sequential fp64 sum of edge e, so the sums of thirty edges share one
+// stream of warp instructions.
 constexpr int kRsWarps = 8;
-constexpr int kRsChunk = 256;
+constexpr int kRsCands = 10;
+constexpr int kRsChunk = 32;
 
 __device__ __forceinline__ double term64(const DevGraph& g, uint32_t h, uint32_t r, uint32_t t, int j) {
     const double a = emb_f64(g.vemb, g.dtype, h, g.d, j);
@@ -1360,50 +1385,59 @@ __device__ __forceinline__ double term64(const DevGraph& g, uint32_t h, uint32_t
 }
 
 __global__ void __launch_bounds__(kRsWarps * 32) k_rescore(const PlanDev* __restrict__ P, DevGraph g) {
-    __shared__ double ys[kRsWarps][3][kRsChunk];
+    __shared__ double ys[kRsWarps][3 * kRsCands][kRsChunk + 1];
+    __shared__ uint32_t eh[kRsWarps][3 * kRsCands], er[kRsWarps][3 * kRsCands], et[kRsWarps][3 * kRsCands];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t total = static_cast<int64_t>(P->nq) * P->band_cap;
+    const int nq = P->nq, cap = P->band_cap;
     const int64_t gw = blockIdx.x * static_cast<int64_t>(kRsWarps) + w;
     const int64_t nw = static_cast<int64_t>(gridDim.x) * kRsWarps;
-    for (int64_t x = gw; x < total; x += nw) {
-        const int q = static_cast<int>(x / P->band_cap);
-        const int i = static_cast<int>(x - static_cast<int64_t>(q) * P->band_cap);
-        if (i >= P->band_cnt[q] || P->dense[q]) {
-            // skip the rest of this query's empty band slots
-            const int64_t next = static_cast<int64_t>(q + 1) * P->band_cap;
-            if (next > x + nw) x += ((next - x - 1) / nw) * nw;
-            continue;
-        }
-        const Cand c = P->band_cand[x];
+    // work unit = (query, group of ten band entries)
+    const int64_t groups_per_q = (cap + kRsCands - 1) / kRsCands;
+    for (int64_t u = gw; u < static_cast<int64_t>(nq) * groups_per_q; u += nw) {
+        const int q = static_cast<int>(u / groups_per_q);
+        const int i0 = static_cast<int>(u - static_cast<int64_t>(q) * groups_per_q) * kRsCands;
+        const int nb = P->band_cnt[q];
+        if (i0 >= nb || P->dense[q]) continue;
+        const int nc = min(kRsCands, nb - i0);
+        const int64_t x0 = static_cast<int64_t>(q) * cap + i0;
         const uint32_t s = P->S[q], t = P->T[q];
-        const int64_t p1 = g.off[s] + c.a_idx;
-        const int64_t p3 = g.roff[t] + c.c_idx;
-        mhr_path p;
-        p.u = g.col[p1];
-        p.r1 = g.rel[p1];
-        p.v = g.rcol[p3];
-        p.r3 = g.rrel[p3];
-        p.r2 = c.r2;
-        p.pad = 0;
-        const uint32_t hh[3] = {s, p.u, p.v}, rr[3] = {p.r1, p.r2, p.r3}, tt[3] = {p.u, p.v, t};
-        double acc = 0.0;
+        mhr_path p;  // lane c < nc: candidate c
+        if (lane < nc) {
+            const Cand c = P->band_cand[x0 + lane];
+            const int64_t p1 = g.off[s] + c.a_idx;
+            const int64_t p3 = g.roff[t] + c.c_idx;
+            p.u = g.col[p1];
+            p.r1 = g.rel[p1];
+            p.v = g.rcol[p3];
+            p.r3 = g.rrel[p3];
+            p.r2 = c.r2;
+            p.pad = 0;
+            eh[w][3 * lane] = s;    er[w][3 * lane] = p.r1;     et[w][3 * lane] = p.u;
+            eh[w][3 * lane + 1] = p.u; er[w][3 * lane + 1] = p.r2; et[w][3 * lane + 1] = p.v;
+            eh[w][3 * lane + 2] = p.v; er[w][3 * lane + 2] = p.r3; et[w][3 * lane + 2] = t;
+        }
+        __syncwarp();
+        const int ne = 3 * nc;
+        double acc = 0.0;  // lane e < ne: sum of edge e
         for (int c0 = 0; c0 < g.d; c0 += kRsChunk) {
             const int n = min(kRsChunk, g.d - c0);
-            for (int j = lane; j < n; j += 32) {
-#pragma unroll
-                for (int e = 0; e < 3; ++e) ys[w][e][j] = term64(g, hh[e], rr[e], tt[e], c0 + j);
+            for (int k = lane; k < ne * n; k += 32) {
+                const int e = k / n, j = k - e * n;
+                ys[w][e][j] = term64(g, eh[w][e], er[w][e], et[w][e], c0 + j);
             }
             __syncwarp();
-            if (lane < 3)
+            if (lane < ne)
                 for (int j = 0; j < n; ++j) acc = __dadd_rn(acc, ys[w][lane][j]);
             __syncwarp();
         }
-        double we = (g.fn == MHR_SCORE_TRANSE_L1) ? __dsub_rn(g.gamma, acc) : acc;
-        const double w1 = __shfl_sync(FULL, we, 0), w2 = __shfl_sync(FULL, we, 1), w3 = __shfl_sync(FULL, we, 2);
-        if (lane == 0) {
+        const double we = (g.fn == MHR_SCORE_TRANSE_L1) ? __dsub_rn(g.gamma, acc) : acc;
+        const int b = 3 * (lane < nc ? lane : 0);
+        const double w1 = __shfl_sync(FULL, we, b), w2 = __shfl_sync(FULL, we, b + 1), w3 = __shfl_sync(FULL, we, b + 2);
+        if (lane < nc) {
             p.score = __dadd_rn(__dadd_rn(w1, w2), w3);
-            P->band_path[x] = p;
+            P->band_path[x0 + lane] = p;
         }
+        __syncwarp();
     }
 }
 
