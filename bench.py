@@ -77,15 +77,37 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_queries(g, S, T, rank: int, workload: str):
+    """Weak scaling: rank 0 keeps the workload's queries, rank r > 0 draws its own
+    set of the same size and recipe (seed r) on the same graph."""
+    import synth
+    if rank == 0:
+        return S, T
+    if workload == "batching":
+        return synth.queries_log_degree(g, len(S), seed=rank)
+    return synth.queries_edge_biased(g, len(S), seed=rank)
+
+
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The job's time is the slowest rank's: all-reduce MAX (no-op at N = 1)."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, ws: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: units all ranks processed / the slowest rank's time."""
+    return units_per_rank * ws * steps / (max_ms / 1000.0)
+
+
 def load_workload(rank: int):
     import synth
     os.environ.setdefault("MHR_SYNTH_CACHE", os.path.join(tempfile.gettempdir(), "mhr_synth_cache"))
     g, S, T, K, spec = synth.workload(WORKLOAD)
-    if rank > 0:  # weak scaling: each rank its own 64 queries on the same graph
-        if WORKLOAD == "batching":
-            S, T = synth.queries_log_degree(g, len(S), seed=rank)
-        else:
-            S, T = synth.queries_edge_biased(g, len(S), seed=rank)
+    S, T = rank_queries(g, S, T, rank, WORKLOAD)
     return g, S, T, K, spec
 
 
@@ -292,25 +314,23 @@ def run_gpu(args):
             dev_ms.append(st["ms_device"])
         torch.cuda.synchronize()
         clk = sampler.stop() if sampler else None
-        el = sum(a.elapsed_time(b) for a, b in ev)
-        t = torch.tensor([el], dtype=torch.float64, device="cuda")
+        el = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), ws, "cuda")
         if ws > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dist.barrier()
-        return float(t.item()), join_ms, dev_ms, st, clk
+        return el, join_ms, dev_ms, st, clk
 
     clocks = ClockSampler(local)
     wall0 = time.perf_counter()
     elapsed_ms, join_ms, dev_ms, stats, clk = timed(opts, args.steps, clocks)
     wall1 = time.perf_counter()
-    value = nq * ws * args.steps / (elapsed_ms / 1000.0)
+    value = job_rate(nq, ws, args.steps, elapsed_ms)
     others = {}
     for of in (["plain", "bound", "chosen"] if args.all_forms else ["plain"]):
         if of == args.form:
             continue
         o_steps = max(3, args.steps // 4)
         o_ms, o_join, o_dev, o_stats, _ = timed(make_opts(of), o_steps)
-        others[of] = {"form": FORM_DESC[of], "value": nq * ws * o_steps / (o_ms / 1000.0),
+        others[of] = {"form": FORM_DESC[of], "value": job_rate(nq, ws, o_steps, o_ms),
                       "ms_per_step": o_ms / o_steps, "join_ms": statistics.mean(o_join),
                       "work_per_step": {k: o_stats[k] for k in ("edges_scanned", "hits", "paths", "pruned_edges")}}
         if of == "plain":
@@ -324,10 +344,7 @@ def run_gpu(args):
         t0 = time.perf_counter()
         h_out, h_n = mhr.mhr_topk_paths_batched(G, S, T, K, opts=opts)
         e2e_times.append(time.perf_counter() - t0)
-    e2e_t = torch.tensor([sum(e2e_times)], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = nq * ws * len(e2e_times) / float(e2e_t.item())
+    e2e_value = job_rate(nq, ws, len(e2e_times), 1000.0 * max_over_ranks(sum(e2e_times), ws, "cuda"))
     # the device run and the host run must agree bit for bit
     dev_paths = mhr.paths_from_device(out, K)
     dn = n_out.cpu().numpy()
