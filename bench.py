@@ -276,6 +276,8 @@ def run_gpu(args):
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
 
+    tuned = {}
+
     def make_opts(form):
         if form == "plain":
             o = {"prune": 0, "order": 0}
@@ -283,8 +285,14 @@ def run_gpu(args):
             o = {"prune": 1, "order": 1, "precision": tc}
         else:
             o = {"prune": 1, "order": 2, "mlp": model, "precision": tc}
-        if args.chunk:
+        if args.chunk > 0:
             o["chunk"] = args.chunk
+        elif args.chunk < 0:
+            # launch shape (work-item size, scan tile) from the library's autotuner,
+            # on this batch, before timing
+            if form not in tuned:
+                tuned[form] = mhr.mhr_autotune(G, dS, dT, K, opts=o, stream=stream)
+            o["chunk"], o["tile"] = tuned[form][0], tuned[form][1]
         return o
 
     opts = make_opts(args.form)
@@ -332,6 +340,8 @@ def run_gpu(args):
         o_ms, o_join, o_dev, o_stats, _ = timed(make_opts(of), o_steps)
         others[of] = {"form": FORM_DESC[of], "value": job_rate(nq, ws, o_steps, o_ms),
                       "ms_per_step": o_ms / o_steps, "join_ms": statistics.mean(o_join),
+                      "chunk": tuned[of][0] if of in tuned else args.chunk,
+                      "tile": tuned[of][1] if of in tuned else None,
                       "work_per_step": {k: o_stats[k] for k in ("edges_scanned", "hits", "paths", "pruned_edges")}}
         if of == "plain":
             o_stats_plain = o_stats
@@ -377,7 +387,11 @@ def run_gpu(args):
                        "middle_edge_screen": "bf16 tensor cores (hi/lo split)" if (tc and args.form != "plain") else "fp32 CUDA cores",
                        "l2": "flushed before every step (256 MiB write, excluded from the step time)",
                        "parallelism": "replicas (each rank its own queries)" if ws > 1 else "single GPU",
-                       "launch": "three CUDA graphs per step (before / join / after)"},
+                       "launch": "three CUDA graphs per step (before / join / after)",
+                       "chunk": opts.get("chunk", "library default"),
+                       "tile": opts.get("tile", "library default"),
+                       "autotune_ms": ({f"{c}x{t}": v for (c, t), v in tuned[args.form][2].items()}
+                                       if args.form in tuned else None)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * nq,
                     "d2h_bytes_per_step": nq * K * 24 + 4 * nq},
             "gpu_launches": KERNELS_PER_STEP * args.steps,
@@ -418,7 +432,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
-    ap.add_argument("--chunk", type=int, default=0, help="middle-join work item size (0 = default)")
+    ap.add_argument("--chunk", type=int, default=-1,
+                    help="middle-join work item size (-1 = autotuned before timing, 0 = library default)")
     ap.add_argument("--workload", default="medium", choices=sorted(WORKLOAD_DESCS),
                     help="medium is the benchmark workload; the others are extra measurements")
     ap.add_argument("--all-forms", type=int, default=1, help="also time the other forms (plain, bound, chosen)")

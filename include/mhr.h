@@ -116,7 +116,8 @@ typedef struct {
 
 /* Query options; a NULL pointer means all defaults (zeros). */
 typedef struct {
-    int32_t chunk;       /* edges per work item of the middle join; 0 = default */
+    int32_t chunk;       /* edges per work item of the middle join: 0 = default (16384), else a
+                            multiple of 32 in [32, 32768] (MHR_EINVAL otherwise) */
     int32_t order;       /* order of intermediate vertices: 0 natural, 1 by score
                             bound, 2 by the learned score of `mlp` */
     int32_t prune;       /* 1 = skip work items, rows and middle edges whose provable
@@ -125,7 +126,9 @@ typedef struct {
                             contraction with hi/lo split and fp32 accumulation (DistMult,
                             at most 16 relations); the fp64 rescoring keeps results exact */
     const mhr_mlp* mlp;  /* order == 2 only */
-    int32_t reserved[2];
+    int32_t tile;        /* 32-edge groups each warp of the middle join scans per step:
+                            0 = default (4), else 4 or 8 (MHR_EINVAL otherwise) */
+    int32_t reserved;
 } mhr_query_opts;
 
 /* Work counters of the last call (optional output). */
@@ -186,6 +189,25 @@ mhr_status mhr_topk_paths_batched(const mhr_graph* g, int32_t nq, const uint32_t
                                   const uint32_t* t, int32_t K, mhr_path* out, int32_t* n_out,
                                   mhr_mem mem, const mhr_query_opts* opts, mhr_stats* stats,
                                   void* cuda_stream);
+
+/*
+ * Launch-shape autotuner for the batched search (the paper has no
+ * counterpart; its OpenMP loops have no tunable shape).  Runs
+ * mhr_topk_paths_batched on the nq queries (s, t; mem applies to both) with
+ * opts and every pair (chunks[i], tiles[j]) as (opts->chunk, opts->tile):
+ * chunks are multiples of 32 in [32, 32768] (NULL: {4096, 8192, 16384, 32768},
+ * n_chunks = 4), tiles are 4 or 8 (NULL: {4, 8}, n_tiles = 2).  Each pair gets
+ * one untimed run, then reps timed runs, timed by CUDA events around the
+ * launch sequence on cuda_stream; ms_out[i * n_tiles + j] (optional, host) =
+ * the fastest of the pair's runs; *best_chunk and *best_tile (host) = the pair
+ * with the lowest time (the first one on ties).  Every run computes the same
+ * result (discarded).  Keeps the winner's buffers and releases the others'.
+ * Synchronous.  MHR_EINVAL on bad arguments or candidates.
+ */
+mhr_status mhr_autotune(const mhr_graph* g, int32_t nq, const uint32_t* s, const uint32_t* t, int32_t K,
+                        mhr_mem mem, const mhr_query_opts* opts, const int32_t* chunks, int32_t n_chunks,
+                        const int32_t* tiles, int32_t n_tiles, int32_t reps, int32_t* best_chunk,
+                        int32_t* best_tile, float* ms_out, void* cuda_stream);
 
 /*
  * Learned ordering (the paper has no learned component; this implements the

@@ -32,6 +32,7 @@ from ._mhr import (  # noqa: F401
     mhr_topk_paths,
     mhr_topk_paths_batched,
     mhr_topk_paths_noalloc,
+    mhr_autotune,
     mhr_training_labels,
     mhr_mlp_features,
     mhr_mlp_forward,

@@ -180,24 +180,25 @@ __global__ void k_init(const PlanDev* __restrict__ P, DevGraph g) {
     if (tid < kCntCount) P->counters[tid] = 0ull;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int c = tid; c < P->grid; c += gridDim.x * blockDim.x) P->cursors[c] = 0ull;
+    for (int c = tid; c < (P->grid + 31) / 32; c += gridDim.x * blockDim.x) P->drained[c] = 0u;
     for (int64_t i = tid; i < 2 * static_cast<int64_t>(nq); i += stride) P->qkey[i] = (i & 1) ? 0u : 0xffffffffu;
     for (int64_t i = tid; i < P->nhist; i += stride) P->hist[i] = 0u;
     for (int64_t i = tid; i < P->item_cap; i += stride) P->item_ub[i] = 0u;
 }
 
-// one group of G lanes per slot: fp32 weight, exclusion, run-head flag
+// fp32 weight, exclusion and run-head flag of every slot.  Each lane resolves
+// one slot of its warp's 32 (query, CSR position, endpoint degree) in
+// parallel; then groups of G lanes score the 32 edges, H = 32 / G at a time.
 __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, DevGraph g) {
     const int lane = threadIdx.x & 31;
-    const int G = P->score_width;
+    const int G = P->score_width, H = 32 / G;
     const int sub = lane & (G - 1);
-    const int64_t group = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / G;
-    const int64_t ngroups = (static_cast<int64_t>(gridDim.x) * blockDim.x) / G;
     const int64_t X = P->X, totA = P->totA;
     const int nq = P->nq;
-    // every lane of a warp runs the same number of iterations (group shuffles)
-    const int64_t iters = (X + ngroups - 1) / ngroups;
-    for (int64_t it = 0; it < iters; ++it) {
-        const int64_t x = group + it * ngroups;
+    const int64_t warp_id = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t base = warp_id * 32; base < X; base += nwarps * 32) {  // warp-uniform
+        const int64_t x = base + lane;
         const bool live = x < X;
         uint32_t s = 0, t = 0, vtx = 0, r = 0, prev = 0xffffffffu, sdeg = 0;
         int64_t k = 0;
@@ -225,13 +226,22 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, D
             }
         }
         const uint32_t hu = sideA ? s : vtx, tv = sideA ? vtx : t;
-        const float w = edge_w32_group(g, hu, r, tv, sub, G);
-        if (live && sub == 0) {
+        float wmine = 0.f;
+        for (int rd = 0; rd < G; ++rd) {
+            const int src = rd * H + lane / G;
+            const uint32_t a = __shfl_sync(0xffffffffu, hu, src);
+            const uint32_t rr = __shfl_sync(0xffffffffu, r, src);
+            const uint32_t b = __shfl_sync(0xffffffffu, tv, src);
+            const float w = edge_w32_group(g, a, rr, b, sub, G);  // dead lanes score vertex 0's rows
+            const float tw = __shfl_sync(0xffffffffu, w, ((lane - rd * H) & (H - 1)) * G);
+            if (lane / H == rd) wmine = tw;
+        }
+        if (live) {
             const bool excl = (vtx == s) || (vtx == t);
             // A vertex with no scan edges can neither be scanned nor be hit, so it
             // never lies on a path: it is dropped from the distinct list.
             const bool head = !excl && sdeg > 0 && (k == 0 || prev != vtx);
-            P->w32[x] = excl ? neg_inf() : w;
+            P->w32[x] = excl ? neg_inf() : wmine;
             P->flag[x] = head ? 1u : 0u;
             P->degv[x] = 0u;
         }
@@ -466,8 +476,11 @@ __global__ void k_order_perm(const PlanDev* __restrict__ P) {
     }
 }
 
+constexpr int kSeedEdges = 2048;    // edges of each query's highest-bound rows done by the seed launch
+constexpr int kSeedMinItems = 2;    // queries with fewer work items are not seeded
+
 // near entries in ordered position: (prefix of scan degree, row start), row
-// bound, and the largest row bound of every work item
+// bound; per work item its descriptor and its largest row bound
 __global__ void k_near(const PlanDev* __restrict__ P, DevGraph g) {
     const int64_t X = P->X;
     const int64_t chunk = P->chunk;
@@ -483,12 +496,31 @@ __global__ void k_near(const PlanDev* __restrict__ P, DevGraph g) {
         P->nearP[x] = make_uint2(static_cast<uint32_t>(pre), e.rowstart);
         const float b = P->bnat[old];
         P->nearB[x] = b;
-        if (P->prune && e.deg > 0) {
-            const uint32_t key = f2key(b);
-            const int64_t i0 = P->item_off[q] + pre / chunk;
-            const int64_t i1 = P->item_off[q] + (pre + e.deg - 1) / chunk;
-            for (int64_t i = i0; i <= i1; ++i) atomicMax(&P->item_ub[i], key);
+        if (e.deg == 0) continue;
+        // Every near entry scans at least one edge, so each edge of the query's
+        // near-edge space lies in exactly one entry: the entry holding an item's
+        // first (last) edge writes that field of the item's descriptor.
+        const int64_t s_near = P->s_near[q];
+        const int64_t pend = pre + e.deg;
+        const uint32_t xi = static_cast<uint32_t>(x - base);
+        const int64_t i0 = P->item_off[q] + pre / chunk;
+        const int64_t i1 = P->item_off[q] + (pend - 1) / chunk;
+        const uint32_t key = f2key(b);
+        // seeded: the seed launch does the query's first kSeedEdges edges
+        const bool seeded = P->prune && P->item_off[q + 1] - P->item_off[q] >= kSeedMinItems;
+        for (int64_t i = i0; i <= i1; ++i) {
+            const int64_t ie0 = (i - P->item_off[q]) * chunk;
+            const int64_t ie1 = min(ie0 + chunk, s_near) - 1;
+            if (ie0 >= pre) {
+                P->item_desc[i].x = static_cast<uint32_t>(q) | (seeded ? 0x80000000u : 0u);
+                P->item_desc[i].y = xi;
+                P->item_desc[i].w = static_cast<uint32_t>(i - P->item_off[q]);
+            }
+            if (ie1 < pend) P->item_desc[i].z = xi;
+            if (P->prune) atomicMax(&P->item_ub[i], key);
         }
+        if (pre <= kSeedEdges - 1 && kSeedEdges - 1 < pend) P->seed_k[q].x = xi;
+        if (pre <= kSeedEdges && kSeedEdges < pend) P->seed_k[q].y = xi;
     }
 }
 
@@ -496,9 +528,6 @@ __global__ void k_near(const PlanDev* __restrict__ P, DevGraph g) {
 // the middle join (persistent)
 // ===========================================================================
 constexpr int kRelCacheVecs = 512;  // 8 KB of fp32 relation embeddings
-constexpr int kSeedEdges = 2048;    // edges of each query's highest-bound rows done by the seed launch
-constexpr int kSeedMinItems = 2;    // queries with fewer work items are not seeded
-
 struct MidSmem {
     uint32_t bm[kMaxBmWords];
     uint32_t rank[kMaxRank + 8];
@@ -522,6 +551,11 @@ struct MidSmem {
     int pool_off;
     uint32_t lt_key;
     float thr_keep;
+    // launch-wide constants and thread-0 counters (kept here to spare registers)
+    double two_err;
+    int64_t total_items;
+    uint32_t f_gk;  // the query's shared K-th score key as read when the item was taken
+    unsigned long long c_scanned, c_hits, c_cands, c_skipped;
 };
 
 // block-wide in-place compaction of the candidate buffer to s32 >= thr
@@ -547,7 +581,7 @@ __device__ void compact_cands(MidSmem& sm, float thr) {
 }
 
 // raise the local threshold from the buffer and the global one, then compact
-__device__ void flush_cands(MidSmem& sm, const PlanDev* __restrict__ P, int K, double two_err) {
+__device__ void flush_cands(MidSmem& sm, const PlanDev* __restrict__ P, int K) {
     const int n = sm.cand_cnt;
     if (n >= K) {
         const uint32_t key = block_select_kth([&](int64_t i) { return f2key(sm.cand[i].s32); }, n, K,
@@ -560,7 +594,7 @@ __device__ void flush_cands(MidSmem& sm, const PlanDev* __restrict__ P, int K, d
     if (threadIdx.x == 0) {
         const uint32_t gk = atomicOr(&P->thr_g[sm.q], 0u);
         if (gk > sm.lt_key) sm.lt_key = gk;
-        sm.thr_keep = keep_threshold(sm.lt_key, two_err);
+        sm.thr_keep = keep_threshold(sm.lt_key, sm.two_err);
     }
     __syncthreads();
     compact_cands(sm, sm.thr_keep);
@@ -575,9 +609,8 @@ __device__ void flush_cands(MidSmem& sm, const PlanDev* __restrict__ P, int K, d
 }
 
 // final flush of the current query into its candidate pool
-__device__ void finish_query(MidSmem& sm, const PlanDev* __restrict__ P, int K, double two_err,
-                             unsigned long long* cand_counter) {
-    if (!sm.local_dense) flush_cands(sm, P, K, two_err);
+__device__ void finish_query(MidSmem& sm, const PlanDev* __restrict__ P, int K) {
+    if (!sm.local_dense) flush_cands(sm, P, K);
     if (threadIdx.x == 0) {
         sm.pool_off = -1;
         if (!sm.local_dense && sm.cand_cnt > 0) {
@@ -585,7 +618,7 @@ __device__ void finish_query(MidSmem& sm, const PlanDev* __restrict__ P, int K, 
             const int off = atomicAdd(&P->pool_cnt[sm.q], n);
             if (off + n > P->pq) atomicExch(&P->dense[sm.q], 1);
             else sm.pool_off = off;
-            *cand_counter += static_cast<unsigned long long>(n);
+            sm.c_cands += static_cast<unsigned long long>(n);
         }
     }
     __syncthreads();
@@ -700,28 +733,10 @@ __device__ __forceinline__ float hit_w32_f32(const DevGraph& g, NearRow& nr, uin
     return transe ? __fsub_rn(g.gamma32, acc) : acc;
 }
 
-// edge range [e0, e1) of a work item in the query's near-edge space; the seed
-// launch does the first kSeedEdges edges of the first item, the main launch the
-// rest of it
 // A query is seeded (its first kSeedEdges edges done by the seed launch) when
 // pruning is on and it has at least kSeedMinItems work items.
 __device__ __forceinline__ bool seeded_query(const PlanDev* __restrict__ P, int q, bool prune) {
     return prune && P->item_off[q + 1] - P->item_off[q] >= kSeedMinItems;
-}
-
-// edge range [e0, e1) of a work item in the query's near-edge space; for a
-// seeded query the seed launch does the first kSeedEdges edges of the first
-// item and the main launch the rest of it
-template <bool SEED>
-__device__ __forceinline__ void item_edges(const PlanDev* __restrict__ P, int64_t item, int q, bool prune,
-                                           int64_t& e0, int64_t& e1) {
-    const int64_t s_near = P->s_near[q];
-    e0 = (item - P->item_off[q]) * P->chunk;
-    e1 = min(e0 + static_cast<int64_t>(P->chunk), s_near);
-    if (e0 == 0 && seeded_query(P, q, prune)) {
-        if (SEED) e1 = min(e1, static_cast<int64_t>(kSeedEdges));
-        else e0 = min(e1, static_cast<int64_t>(kSeedEdges));
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -819,6 +834,36 @@ __device__ float tc_batch_w2(const DevGraph& g, const uint16_t* __restrict__ wsp
     return w;
 }
 
+// Thread 0 of a join CTA: the next work item of its own contiguous range, else
+// of the following ranges (stealing).  A bit map marks ranges found drained so
+// that a thief skips up to 32 of them with one read.
+__device__ __forceinline__ int64_t take_item(const PlanDev* __restrict__ P, int64_t total_items, int& victim,
+                                             unsigned long long& probes) {
+    const int grid = static_cast<int>(gridDim.x);
+    while (victim < grid) {
+        const int v = (static_cast<int>(blockIdx.x) + victim) % grid;
+        if (victim > 0) {
+            const uint32_t w = __ldcg(P->drained + (v >> 5)) >> (v & 31);
+            if (w & 1u) {
+                // bits at and above `grid` are never set, so the run stays inside [v, grid)
+                const uint32_t nw = ~w;
+                victim += nw ? __ffs(nw) - 1 : 32 - (v & 31);
+                continue;
+            }
+        }
+        ++probes;
+        const int64_t lo = total_items * v / grid;
+        const int64_t hi = total_items * (v + 1) / grid;
+        if (lo < hi) {
+            const int64_t idx = static_cast<int64_t>(atomicAdd(&P->cursors[v], 1ull));
+            if (lo + idx < hi) return lo + idx;
+        }
+        atomicOr(&P->drained[v >> 5], 1u << (v & 31));
+        ++victim;
+    }
+    return total_items;
+}
+
 // SEED: with bound pruning on, a first launch processes only the first work
 // item of every query (its highest-bound rows when rows are ordered), so the
 // shared K-th score of every query is set before the main launch starts.
@@ -830,10 +875,8 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
     const int K = P->K;
     const int nq = P->nq;
     const int sigma = P->sigma;
-    const double two_err = 2.0 * P->err_path;
-    const int64_t total_items = P->item_off[nq];
     Hit* hits = P->hits + static_cast<int64_t>(blockIdx.x) * kMaxChunk;
-    unsigned long long n_scanned = 0, n_hits = 0, n_cands = 0, n_paths_w = 0, n_pruned = 0, n_skipped = 0;
+    uint32_t n_paths_w = 0, n_pruned = 0;  // per lane
     const bool prune = P->prune != 0;
     const float slack = P->prune_slack;
     if (SEED && !prune) return;
@@ -849,14 +892,29 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
             tph = now__;                              \
         }                                             \
     } while (0)
+    // per warp: own cycles in the scan and score loops (before the closing barrier);
+    // thread 0: items taken, fetch-loop iterations, ranges probed, query switches
+    unsigned long long wt_scan = 0, wt_score = 0, t_w = 0;
+    unsigned long long c_items = 0, c_iter = 0, c_probe = 0, c_switch = 0;
+#define MHR_WSTART() (t_w = clock64())
+#define MHR_WEND(acc) ((acc) += clock64() - t_w)
+#define MHR_COUNT(c) (++(c))
 #else
 #define MHR_PHASE(i) \
     do {             \
     } while (0)
+#define MHR_WSTART() ((void)0)
+#define MHR_WEND(acc) ((void)0)
+#define MHR_COUNT(c) ((void)0)
 #endif
     int cur_q = -1;
     int victim = 0;  // thread 0: offset of the range it currently drains
-    if (threadIdx.x == 0) sm.q = -1;
+    if (threadIdx.x == 0) {
+        sm.q = -1;
+        sm.two_err = 2.0 * P->err_path;
+        sm.total_items = P->item_off[nq];
+        sm.c_scanned = sm.c_hits = sm.c_cands = sm.c_skipped = 0ull;
+    }
     // fast hit scorer: fp32 rows of at most 2G vectors per lane group
     const int vec4 = g.d / 4;
     const bool fast = g.dtype == MHR_F32 && (g.d & 3) == 0 && vec4 <= 2 * P->score_width;
@@ -868,12 +926,19 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
 
     for (;;) {
         if (threadIdx.x == 0) {
+            // Take the next work item that cannot be skipped, and prepare it: the
+            // item is skipped without touching the CTA's query state when its
+            // query is being recomputed exactly, when the seed launch did all of
+            // it, or when no row of it can reach the query's kept band.
+            const int64_t total_items = sm.total_items;
             int64_t it = total_items;
             int iq = -1;
+            unsigned long long probes = 0;
             for (;;) {
+                MHR_COUNT(c_iter);
                 it = total_items;
                 if (SEED) {
-                    // one item per query: the first one
+                    // one item per seeded query: its first one
                     if (prune) {
                         for (;;) {
                             const int qq = static_cast<int>(atomicAdd(&P->counters[kCntSeed], 1ull));
@@ -885,89 +950,77 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                         }
                     }
                 } else {
-                    // Items are laid out query by query; CTA b owns the contiguous
-                    // range [b*N/grid, (b+1)*N/grid) so it meets few queries, then
-                    // steals from the following ranges once its own is drained.
-                    while (victim < static_cast<int>(gridDim.x)) {
-                        // every item taken already: stop probing the other ranges
-                        if (victim > 0 &&
-                            atomicAdd(&P->counters[kCntItem], 0ull) >= static_cast<unsigned long long>(total_items))
-                            break;
-                        const int v = (blockIdx.x + victim) % gridDim.x;
-                        const int64_t lo = total_items * v / gridDim.x;
-                        const int64_t hi = total_items * (v + 1) / gridDim.x;
-                        if (lo < hi) {
-                            const int64_t idx = static_cast<int64_t>(atomicAdd(&P->cursors[v], 1ull));
-                            if (lo + idx < hi) {
-                                it = lo + idx;
-                                atomicAdd(&P->counters[kCntItem], 1ull);
-                                break;
-                            }
-                        }
-                        ++victim;
-                    }
+                    it = take_item(P, total_items, victim, probes);
                 }
                 if (it >= total_items) break;
-                iq = static_cast<int>(upper_bound_i64(P->item_off, nq + 1, it) - 1);
-                // skip without touching the CTA's query state: the query is being
-                // recomputed exactly, the seed launch did all of this item, or no
-                // row of the item can reach the query's kept band
-                bool skip = atomicOr(&P->dense[iq], 0) != 0;
+                const uint4 dsc = P->item_desc[it];
+                const uint32_t ub = P->item_ub[it];
+                iq = static_cast<int>(dsc.x & 0x7fffffffu);
+                const bool seeded = (dsc.x >> 31) != 0u;
+                const int64_t li = dsc.w;
+                const int dense = __ldcg(P->dense + iq);
+                uint32_t gk = __ldcg(P->thr_g + iq);
+                const int64_t s_near = P->s_near[iq];
+                if (iq == sm.q && sm.lt_key > gk) gk = sm.lt_key;
+                const int64_t chunk = P->chunk;
+                const int64_t first = min(chunk, s_near);  // edges of the query's first item
+                bool skip = dense != 0;
                 if (!SEED && prune && !skip) {
-                    if (it == P->item_off[iq] && seeded_query(P, iq, prune) &&
-                        min(static_cast<int64_t>(P->chunk), P->s_near[iq]) <= kSeedEdges)
+                    if (li == 0 && seeded && first <= kSeedEdges) {
                         skip = true;  // the seed launch did all of it
-                    else {
-                        uint32_t gk = atomicOr(&P->thr_g[iq], 0u);
-                        if (iq == sm.q && sm.lt_key > gk) gk = sm.lt_key;
-                        if (gk != 0u && __fadd_ru(key2f(P->item_ub[it]), P->prune_slack) < keep_threshold(gk, two_err)) {
-                            skip = true;
-                            ++n_skipped;
-                        }
+                    } else if (gk != 0u && __fadd_ru(key2f(ub), P->prune_slack) < keep_threshold(gk, sm.two_err)) {
+                        skip = true;
+                        ++sm.c_skipped;
                     }
                 }
-                if (!skip) break;
+                if (skip) continue;
+                // edge range and the near entries holding its first and last edge
+                int64_t e0 = li * chunk, e1 = min(e0 + chunk, s_near);
+                uint32_t k0 = dsc.y, k1 = dsc.z;
+                if (li == 0 && seeded && first > kSeedEdges) {
+                    const uint2 sk = P->seed_k[iq];
+                    if (SEED) {
+                        e1 = kSeedEdges;  // last edge kSeedEdges - 1
+                        k1 = sk.x;
+                    } else {
+                        e0 = kSeedEdges;  // first edge kSeedEdges
+                        k0 = sk.y;
+                    }
+                }
+                sm.e0 = static_cast<uint32_t>(e0);
+                sm.e1 = static_cast<uint32_t>(e1);
+                sm.k0 = k0;
+                sm.k1 = k1;
+                sm.f_gk = gk;
+                break;
             }
+#ifdef MHR_PHASE_TIMING
+            c_probe += probes;
+#endif
             sm.item = it;
             sm.skip = iq;  // temporarily: the item's query
+            if (it < total_items) MHR_COUNT(c_items);
         }
         __syncthreads();
         const int64_t item = sm.item;
-        if (item >= total_items) break;
+        if (item >= sm.total_items) break;
         const int q = sm.skip;
         __syncthreads();
         if (q != cur_q) {
-            if (cur_q >= 0) finish_query(sm, P, K, two_err, &n_cands);
+            if (cur_q >= 0) finish_query(sm, P, K);
             setup_query(sm, P, q);
             cur_q = q;
+            MHR_COUNT(c_switch);
         }
         MHR_PHASE(0);
         if (threadIdx.x == 0) {
-            sm.skip = sm.local_dense || atomicOr(&P->dense[q], 0) != 0;
-            const uint32_t gk = atomicOr(&P->thr_g[q], 0u);
+            sm.skip = sm.local_dense;
+            const uint32_t gk = sm.f_gk;
             if (gk > sm.lt_key) {
                 sm.lt_key = gk;
-                sm.thr_keep = keep_threshold(gk, two_err);
+                sm.thr_keep = keep_threshold(gk, sm.two_err);
             }
-            int64_t e0, e1;
-            item_edges<SEED>(P, item, q, prune, e0, e1);
-            sm.e0 = static_cast<uint32_t>(e0);
-            sm.e1 = static_cast<uint32_t>(e1);
             sm.hit_cnt = 0;
-        } else if (threadIdx.x == 32 || threadIdx.x == 64) {
-            // largest near index whose prefix is <= e (e = e0 or e1 - 1)
-            int64_t e0, e1;
-            item_edges<SEED>(P, item, q, prune, e0, e1);
-            const int64_t e = threadIdx.x == 32 ? e0 : e1 - 1;
-            const int64_t nb = P->dir[q] ? P->a_off[q] : P->totA + P->c_off[q];
-            int lo = 0, hi = P->near_cnt[q];
-            while (lo + 1 < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (static_cast<int64_t>(P->nearP[nb + mid].x) <= e) lo = mid;
-                else hi = mid;
-            }
-            if (threadIdx.x == 32) sm.k0 = lo;
-            else sm.k1 = lo;
         }
         __syncthreads();
         if (sm.skip) continue;
@@ -989,7 +1042,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         }
         __syncthreads();
         {
-            // inclusive prefix max over <= 512 entries (one per thread)
+            // inclusive prefix max over <= 1024 entries (one per thread)
             uint32_t v = threadIdx.x < ngroups ? sm.gmap[threadIdx.x] : 0u;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -1020,6 +1073,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         const int far_cnt = sm.far_cnt;
         const float* nearB = P->nearB + sm.near_base;
         const float thr_scan = sm.thr_keep;
+        MHR_WSTART();
         for (int gb = warp * UNROLL; gb < ngroups; gb += kMidWarps * UNROLL) {
             uint2 ne[UNROLL];
             uint32_t kk[UNROLL];
@@ -1120,13 +1174,14 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                 }
             }
         }
+        MHR_WEND(wt_scan);
         if (threadIdx.x == 0) sm.round_cnt = sm.cand_cnt;
         __syncthreads();
         MHR_PHASE(2);
         const int nh = sm.hit_cnt;
         if (threadIdx.x == 0) {
-            n_scanned += e1 - e0;
-            n_hits += static_cast<unsigned long long>(nh);
+            sm.c_scanned += e1 - e0;
+            sm.c_hits += static_cast<unsigned long long>(nh);
         }
 
         // --- score hits; keep paths that can still reach the top K.
@@ -1149,6 +1204,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         NearRow nrow;
         nrow.id = 0xffffffffu;
         for (;;) {
+            MHR_WSTART();
             const int budget = (kCandCap - sm.round_cnt) / kMidWarps;
             int used = 0;
             bool done = true;
@@ -1180,11 +1236,11 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                             hcl = ec.run_len;
                             mw1 = ea.maxw;
                             mw3 = ec.maxw;
-                            n_paths_w += static_cast<unsigned long long>(hal) * hcl;
+                            n_paths_w += hal * hcl;
                             alive = true;
                             if (prune) {
-                                // w2 <= max weight of the scanned vertex's adjacent edges
-                                const float mw2 = sm.dir ? g.maxw_out[hu] : g.maxw_in[hv];
+                                // w2 <= the largest weight of any out-edge of u and of any in-edge of v
+                                const float mw2 = fminf(g.maxw_out[hu], g.maxw_in[hv]);
                                 if (__fadd_ru(__fadd_rn(__fadd_rn(mw1, mw2), mw3), slack) < thr) {
                                     alive = false;
                                     ++n_pruned;
@@ -1239,46 +1295,75 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                         loaded = true;
                         slice = 0;
                     }
-                    // each lane walks the (r1, r3) combinations of its own hit
+                    // The (r1, r3) combinations of the pending hits, flattened: lane h's
+                    // remaining combinations take positions [excl, excl + rem) of one
+                    // sequence that the warp walks 32 at a time, so a hit with many
+                    // parallel edges does not serialise the warp.
                     bool stop = false;
-                    for (;;) {
-                        const bool act = (pend >> lane) & 1u;
-                        if (!__any_sync(FULL, act)) break;
-                        bool keep = false;
-                        Cand cd;
-                        if (act) {
-                            uint32_t i = slice, j = 0;
-                            if (hcl != 1) {
-                                i = slice / hcl;
-                                j = slice - i * hcl;
+                    {
+                        const bool mine = (pend >> lane) & 1u;
+                        const uint32_t ncomb = hal * hcl;
+                        const uint32_t rem = mine ? ncomb - slice : 0u;
+                        uint32_t incl = rem;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const uint32_t y = __shfl_up_sync(FULL, incl, o);
+                            if (lane >= o) incl += y;
+                        }
+                        const uint32_t total = __shfl_sync(FULL, incl, 31);
+                        const uint32_t excl = incl - rem;
+                        uint32_t c0 = 0;
+                        for (; c0 < total; c0 += 32) {
+                            const uint32_t f = c0 + lane;
+                            // owner of position f: the number of lanes whose inclusive prefix is <= f
+                            int own = 0;
+#pragma unroll
+                            for (int step = 16; step > 0; step >>= 1) {
+                                const uint32_t pv = __shfl_sync(FULL, incl, own + step - 1);
+                                if (pv <= f) own += step;
                             }
-                            const float s32 = __fadd_rn(__fadd_rn(w1s[has + i], hw2), w3s[hcs + j]);
-                            keep = s32 >= thr;
-                            cd.s32 = s32;
-                            cd.a_idx = has + i;
-                            cd.c_idx = hcs + j;
-                            cd.r2 = static_cast<uint16_t>(hr2);
-                            cd.pad = 0;
+                            const uint32_t o_excl = __shfl_sync(FULL, excl, own);
+                            const uint32_t o_slice = __shfl_sync(FULL, slice, own);
+                            const uint32_t o_hcl = __shfl_sync(FULL, hcl, own);
+                            const uint32_t o_has = __shfl_sync(FULL, has, own);
+                            const uint32_t o_hcs = __shfl_sync(FULL, hcs, own);
+                            const uint32_t o_r2 = __shfl_sync(FULL, hr2, own);
+                            const float o_w2 = __shfl_sync(FULL, hw2, own);
+                            bool keep = false;
+                            Cand cd;
+                            if (f < total) {
+                                const uint32_t sl = o_slice + (f - o_excl);
+                                uint32_t i = sl, j = 0;
+                                if (o_hcl != 1) {
+                                    i = sl / o_hcl;
+                                    j = sl - i * o_hcl;
+                                }
+                                const float s32 = __fadd_rn(__fadd_rn(w1s[o_has + i], o_w2), w3s[o_hcs + j]);
+                                keep = s32 >= thr;
+                                cd.s32 = s32;
+                                cd.a_idx = o_has + i;
+                                cd.c_idx = o_hcs + j;
+                                cd.r2 = static_cast<uint16_t>(o_r2);
+                                cd.pad = 0;
+                            }
+                            const unsigned bal = __ballot_sync(FULL, keep);
+                            const int nk2 = __popc(bal);
+                            if (used + nk2 > budget) {
+                                stop = true;
+                                break;
+                            }
+                            if (nk2) {
+                                int base = 0;
+                                const int leader = __ffs(bal) - 1;
+                                if (lane == leader) base = atomicAdd(&sm.cand_cnt, nk2);
+                                base = __shfl_sync(FULL, base, leader);
+                                if (keep) sm.cand[base + __popc(bal & lanemask_lt())] = cd;
+                            }
+                            used += nk2;
                         }
-                        const unsigned bal = __ballot_sync(FULL, keep);
-                        const int nk2 = __popc(bal);
-                        if (used + nk2 > budget) {
-                            stop = true;
-                            break;
-                        }
-                        if (nk2) {
-                            int base = 0;
-                            const int leader = __ffs(bal) - 1;
-                            if (lane == leader) base = atomicAdd(&sm.cand_cnt, nk2);
-                            base = __shfl_sync(FULL, base, leader);
-                            if (keep) sm.cand[base + __popc(bal & lanemask_lt())] = cd;
-                        }
-                        used += nk2;
-                        if (act) {
-                            ++slice;
-                            if (slice >= hal * hcl) pend &= ~(1u << lane);
-                        }
-                        pend = __ballot_sync(FULL, (pend >> lane) & 1u);
+                        // positions [0, c0) are done
+                        if (mine) slice += c0 > excl ? min(c0 - excl, rem) : 0u;
+                        pend = __ballot_sync(FULL, mine && slice < ncomb);
                     }
                     if (stop) {
                         done = false;
@@ -1288,31 +1373,52 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                     b += kMidWarps;
                 }
             }
+            MHR_WEND(wt_score);
             if (!__syncthreads_or(done ? 0 : 1)) break;
-            flush_cands(sm, P, K, two_err);
+            flush_cands(sm, P, K);
         }
         __syncthreads();
         if (!sm.local_dense && (sm.lt_key == 0u ? sm.cand_cnt >= K : sm.cand_cnt > kCandCap / 2))
-            flush_cands(sm, P, K, two_err);
+            flush_cands(sm, P, K);
         MHR_PHASE(3);
     }
-    if (cur_q >= 0) finish_query(sm, P, K, two_err, &n_cands);
+    if (cur_q >= 0) finish_query(sm, P, K);
     MHR_PHASE(0);
 #ifdef MHR_PHASE_TIMING
     if (threadIdx.x == 0) printf("MHR_PHASE %d %llu %llu %llu %llu\n", blockIdx.x, ph[0], ph[1], ph[2], ph[3]);
+    {
+        unsigned long long* wr = reinterpret_cast<unsigned long long*>(sm.red);
+        __syncthreads();
+        if (threadIdx.x < 4) wr[threadIdx.x] = 0ull;
+        __syncthreads();
+        if (lane == 0) {
+            atomicMax(&wr[0], wt_scan);
+            atomicAdd(&wr[1], wt_scan);
+            atomicMax(&wr[2], wt_score);
+            atomicAdd(&wr[3], wt_score);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            printf("MHR_WARPS %d %d items %llu iters %llu probes %llu switches %llu scan_max %llu scan_mean %llu "
+                   "score_max %llu score_mean %llu\n",
+                   blockIdx.x, SEED ? 1 : 0, c_items, c_iter, c_probe, c_switch, wr[0], wr[1] / kMidWarps, wr[2],
+                   wr[3] / kMidWarps);
+    }
 #endif
     if (threadIdx.x == 0) {
-        atomicAdd(&P->counters[kCntScanned], n_scanned);
-        atomicAdd(&P->counters[kCntHits], n_hits);
-        atomicAdd(&P->counters[kCntCands], n_cands);
-        if (n_skipped) atomicAdd(&P->counters[kCntSkippedItems], n_skipped);
+        atomicAdd(&P->counters[kCntScanned], sm.c_scanned);
+        atomicAdd(&P->counters[kCntHits], sm.c_hits);
+        atomicAdd(&P->counters[kCntCands], sm.c_cands);
+        if (sm.c_skipped) atomicAdd(&P->counters[kCntSkippedItems], sm.c_skipped);
     }
+    unsigned long long wp = n_pruned, wq = n_paths_w;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n_pruned += __shfl_xor_sync(FULL, n_pruned, o);
-    if (lane == 0 && n_pruned) atomicAdd(&P->counters[kCntPruned], n_pruned);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n_paths_w += __shfl_xor_sync(FULL, n_paths_w, o);
-    if (lane == 0 && n_paths_w) atomicAdd(&P->counters[kCntPaths], n_paths_w);
+    for (int o = 16; o > 0; o >>= 1) {
+        wp += __shfl_xor_sync(FULL, wp, o);
+        wq += __shfl_xor_sync(FULL, wq, o);
+    }
+    if (lane == 0 && wp) atomicAdd(&P->counters[kCntPruned], wp);
+    if (lane == 0 && wq) atomicAdd(&P->counters[kCntPaths], wq);
 }
 
 // ===========================================================================
@@ -1652,7 +1758,8 @@ __global__ void k_dump_labels(const PlanDev* __restrict__ P, int64_t cap, uint32
 // host side: plans (buffers + captured graph) per (nq, K, chunk)
 // ===========================================================================
 struct Plan {
-    int nq = 0, K = 0, chunk = 0, grid = 0, precision = 0;
+    int nq = 0, K = 0, chunk = 0, grid = 0, precision = 0, tile = kDefaultTile;
+    int expand_per_sm = 8;  // resident k_expand blocks per SM
     PlanDev h{};
     unsigned char* dregion = nullptr;  // [PlanDev][S][T][a_off][c_off]
     size_t region_bytes = 0;
@@ -1688,7 +1795,7 @@ struct Plan {
 };
 
 struct PlanCache {
-    std::map<std::tuple<int, int, int, int>, Plan*> plans;
+    std::map<std::tuple<int, int, int, int, int>, Plan*> plans;  // (nq, K, chunk, precision, tile)
     ~PlanCache() {
         for (auto& kv : plans) delete kv.second;
     }
@@ -1800,7 +1907,8 @@ static mhr_status ensure_items(Plan* p, int64_t cap) {
     if (cap <= p->h.item_cap && p->h.item_ub) return MHR_OK;
     cap = std::max(cap, 2 * p->h.item_cap);
     void* mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, sizeof(uint32_t) * cap);
+    const size_t o_desc = align_up(sizeof(uint32_t) * cap, 256);
+    cudaError_t e = cudaMalloc(&mem, o_desc + sizeof(uint4) * cap);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (work-item bounds)");
     if (p->item_mem) {
         cudaDeviceSynchronize();
@@ -1808,6 +1916,7 @@ static mhr_status ensure_items(Plan* p, int64_t cap) {
     }
     p->item_mem = mem;
     p->h.item_ub = static_cast<uint32_t*>(mem);
+    p->h.item_desc = reinterpret_cast<uint4*>(static_cast<unsigned char*>(mem) + o_desc);
     p->h.item_cap = cap;
     return MHR_OK;
 }
@@ -1819,7 +1928,7 @@ static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int
     const int64_t* nX = reinterpret_cast<const int64_t*>(p->dregion + offsetof(PlanDev, X));
     if (part == 0) {
         k_init<<<sms * 2, 256, 0, st>>>(d, g);
-        k_expand<<<sms * 8, 256, 0, st>>>(d, g);
+        k_expand<<<sms * p->expand_per_sm, 256, 0, st>>>(d, g);
         cudaError_t e = device_excl_scan<uint32_t>(p->h.flag, nX, p->h.partials, p->h.scan1, st);
         if (e != cudaSuccess) return e;
         k_lists<<<sms * 4, 256, 0, st>>>(d, g);
@@ -1837,12 +1946,23 @@ static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int
         if (e != cudaSuccess) return e;
         k_near<<<sms * 4, 256, 0, st>>>(d, g);
     } else if (part == 1) {
-        if (p->precision) {
-            k_middle<kUnroll, true, true><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
-            k_middle<kUnroll, false, true><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
+        const size_t sb = mid_smem_bytes();
+        if (p->tile == 8) {
+            if (p->precision) {
+                k_middle<8, true, true><<<p->grid, kMidThreads, sb, st>>>(d, g);
+                k_middle<8, false, true><<<p->grid, kMidThreads, sb, st>>>(d, g);
+            } else {
+                k_middle<8, true, false><<<p->grid, kMidThreads, sb, st>>>(d, g);
+                k_middle<8, false, false><<<p->grid, kMidThreads, sb, st>>>(d, g);
+            }
         } else {
-            k_middle<kUnroll, true, false><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
-            k_middle<kUnroll, false, false><<<p->grid, kMidThreads, mid_smem_bytes(), st>>>(d, g);
+            if (p->precision) {
+                k_middle<4, true, true><<<p->grid, kMidThreads, sb, st>>>(d, g);
+                k_middle<4, false, true><<<p->grid, kMidThreads, sb, st>>>(d, g);
+            } else {
+                k_middle<4, true, false><<<p->grid, kMidThreads, sb, st>>>(d, g);
+                k_middle<4, false, false><<<p->grid, kMidThreads, sb, st>>>(d, g);
+            }
         }
     } else {
         k_merge1<<<std::min(p->nq, sms * 2), 1024, 0, st>>>(d);
@@ -1905,9 +2025,10 @@ static int choose_sigma(int64_t n) {
     return sigma;
 }
 
-static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precision, Plan** out) {
+static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precision, int tile, Plan** out) {
     Plan* p = new Plan();
     p->nq = nq;
+    p->tile = tile;
     p->K = K;
     p->chunk = chunk;
     p->precision = precision;
@@ -1938,6 +2059,7 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precisio
     if ((rc = plan_alloc(p, &h.item_off, nq + 1)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.near_off, nq + 1)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.thr_g, nq)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.seed_k, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.qmax, 2 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.qkey, 2 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.hist, 256 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);
@@ -1955,6 +2077,7 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precisio
     if ((rc = plan_alloc(p, &h.counters, kCntCount)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.partials, kScanGrid + 1)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.cursors, p->grid)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.drained, (p->grid + 31) / 32)) != MHR_OK) return bail(rc);
     h.grid = p->grid;
     const RegionLayout L = region_layout(nq);
     p->region_bytes = L.total;
@@ -1977,12 +2100,23 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precisio
     {
         const int sb = static_cast<int>(mid_smem_bytes());
         const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        e = cudaFuncSetAttribute(k_middle<kUnroll, true, false>, a, sb);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_middle<kUnroll, false, false>, a, sb);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_middle<kUnroll, true, true>, a, sb);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_middle<kUnroll, false, true>, a, sb);
+        e = cudaFuncSetAttribute(k_middle<4, true, false>, a, sb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_middle<4, false, false>, a, sb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_middle<4, true, true>, a, sb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_middle<4, false, true>, a, sb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_middle<8, true, false>, a, sb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_middle<8, false, false>, a, sb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_middle<8, true, true>, a, sb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_middle<8, false, true>, a, sb);
     }
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaFuncSetAttribute (middle join)"));
+    {
+        // one resident wave of the grid-stride expansion kernel
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_expand, 256, 0) == cudaSuccess && nb > 0)
+            p->expand_per_sm = nb;
+        cudaGetLastError();
+    }
     e = cudaFuncSetAttribute(k_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(exact_smem_bytes()));
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaFuncSetAttribute (exact)"));
@@ -1993,9 +2127,9 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precisio
     return MHR_OK;
 }
 
-static mhr_status get_plan(mhr_graph* G, int nq, int K, int chunk, int precision, Plan** out) {
+static mhr_status get_plan(mhr_graph* G, int nq, int K, int chunk, int precision, int tile, Plan** out) {
     if (!G->plans) G->plans = new PlanCache();
-    auto key = std::make_tuple(nq, K, chunk, precision);
+    auto key = std::make_tuple(nq, K, chunk, precision, tile);
     auto it = G->plans->plans.find(key);
     if (it != G->plans->plans.end()) {
         *out = it->second;
@@ -2007,7 +2141,7 @@ static mhr_status get_plan(mhr_graph* G, int nq, int K, int chunk, int precision
         G->plans->plans.erase(G->plans->plans.begin());
     }
     Plan* p = nullptr;
-    MHR_TRY(make_plan(G, nq, K, chunk, precision, &p));
+    MHR_TRY(make_plan(G, nq, K, chunk, precision, tile, &p));
     G->plans->plans[key] = p;
     *out = p;
     return MHR_OK;
@@ -2017,14 +2151,16 @@ static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint
                             const mhr_query_opts* opts, cudaStream_t st, Plan** plan_out, bool label = false) {
     int chunk = (opts && opts->chunk > 0) ? opts->chunk : kDefaultChunk;
     if (chunk > kMaxChunk || chunk < 32 || (chunk & 31))
-        return fail(MHR_EINVAL, "opts->chunk must be a multiple of 32 in [32, 16384]");
+        return fail(MHR_EINVAL, "opts->chunk must be a multiple of 32 in [32, 32768]");
     const int precision = opts ? opts->precision : 0;
     if (precision != 0 && precision != 1) return fail(MHR_EINVAL, "opts->precision must be 0 or 1");
+    const int tile = (opts && opts->tile) ? opts->tile : kDefaultTile;
+    if (tile != 4 && tile != 8) return fail(MHR_EINVAL, "opts->tile must be 0, 4 or 8");
     if (precision == 1 && (G->fn != MHR_SCORE_DISTMULT || G->dg.R > 16 || !G->wsplit))
         return fail(MHR_EINVAL, "the tensor-core screen (precision 1) needs DistMult and at most 16 relations");
     if (precision == 1 && label) return fail(MHR_EINVAL, "label runs use the plain search");
     Plan* p = nullptr;
-    MHR_TRY(get_plan(G, nq, K, chunk, precision, &p));
+    MHR_TRY(get_plan(G, nq, K, chunk, precision, tile, &p));
     // sizes from the host copy of the row starts
     const RegionLayout L = region_layout(nq);
     if (p->h2d_pending) {
@@ -2147,6 +2283,79 @@ extern "C" mhr_status mhr_topk_paths_batched(const mhr_graph* gc, int32_t nq, co
     if (stats) {
         *stats = mhr_stats{};
         MHR_TRY(read_stats(p, st, stats));
+    }
+    return MHR_OK;
+}
+
+// Autotuner of the join's launch shape: every (work-item size, scan tile)
+// candidate runs the same batch (results do not depend on either), timed by
+// the plan's own events; the plans of the losing candidates are released.
+extern "C" mhr_status mhr_autotune(const mhr_graph* gc, int32_t nq, const uint32_t* s, const uint32_t* t, int32_t K,
+                                   mhr_mem mem, const mhr_query_opts* opts, const int32_t* chunks, int32_t n_chunks,
+                                   const int32_t* tiles, int32_t n_tiles, int32_t reps, int32_t* best_chunk,
+                                   int32_t* best_tile, float* ms_out, void* cuda_stream) {
+    MHR_TRY(check_graph(gc));
+    mhr_graph* G = const_cast<mhr_graph*>(gc);
+    static const int32_t kChunks[4] = {4096, 8192, 16384, 32768};
+    static const int32_t kTiles[2] = {4, 8};
+    if (!chunks) {
+        chunks = kChunks;
+        n_chunks = 4;
+    }
+    if (!tiles) {
+        tiles = kTiles;
+        n_tiles = 2;
+    }
+    if (nq < 1 || !s || !t || !best_chunk || !best_tile || n_chunks < 1 || n_tiles < 1 || reps < 1)
+        return fail(MHR_EINVAL, "bad autotune arguments");
+    if (K < 1) return fail(MHR_EINVAL, "K must be >= 1");
+    if (K > MHR_K_MAX) return fail(MHR_ERANGE, "K exceeds MHR_K_MAX");
+    if (mem != MHR_MEM_HOST && mem != MHR_MEM_DEVICE) return fail(MHR_EINVAL, "unknown mem kind");
+    for (int i = 0; i < n_chunks; ++i)
+        if (chunks[i] > kMaxChunk || chunks[i] < 32 || (chunks[i] & 31))
+            return fail(MHR_EINVAL, "chunk candidates must be multiples of 32 in [32, 32768]");
+    for (int i = 0; i < n_tiles; ++i)
+        if (tiles[i] != 4 && tiles[i] != 8) return fail(MHR_EINVAL, "tile candidates must be 4 or 8");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<uint32_t> hs(nq), ht(nq);
+    MHR_CUDA_TRY(cudaMemcpyAsync(hs.data(), s, sizeof(uint32_t) * nq, cudaMemcpyDefault, st));
+    MHR_CUDA_TRY(cudaMemcpyAsync(ht.data(), t, sizeof(uint32_t) * nq, cudaMemcpyDefault, st));
+    MHR_CUDA_TRY(cudaStreamSynchronize(st));
+    mhr_query_opts o = opts ? *opts : mhr_query_opts{};
+    int best = -1;
+    float best_ms = 0.f;
+    for (int i = 0; i < n_chunks * n_tiles; ++i) {
+        o.chunk = chunks[i / n_tiles];
+        o.tile = tiles[i % n_tiles];
+        Plan* p = nullptr;
+        MHR_TRY(run_batch(G, nq, hs.data(), ht.data(), K, &o, st, &p));  // warm-up (capture, buffers)
+        float ms = 0.f;
+        for (int r = 0; r < reps; ++r) {
+            MHR_TRY(run_batch(G, nq, hs.data(), ht.data(), K, &o, st, &p));
+            mhr_stats sts{};
+            MHR_TRY(read_stats(p, st, &sts));
+            if (sts.ms_device < 0) return fail(MHR_ECUDA, "autotune: event timing failed");
+            ms = r == 0 ? static_cast<float>(sts.ms_device) : std::min(ms, static_cast<float>(sts.ms_device));
+        }
+        if (ms_out) ms_out[i] = ms;
+        if (best < 0 || ms < best_ms) {
+            best = i;
+            best_ms = ms;
+        }
+    }
+    *best_chunk = chunks[best / n_tiles];
+    *best_tile = tiles[best % n_tiles];
+    // keep only the winner's plan
+    MHR_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < n_chunks * n_tiles; ++i) {
+        const int c = chunks[i / n_tiles], tl = tiles[i % n_tiles];
+        if (c == *best_chunk && tl == *best_tile) continue;
+        auto it = G->plans->plans.find(std::make_tuple(static_cast<int>(nq), static_cast<int>(K), c,
+                                                       static_cast<int>(o.precision), tl));
+        if (it != G->plans->plans.end()) {
+            delete it->second;
+            G->plans->plans.erase(it);
+        }
     }
     return MHR_OK;
 }

@@ -11,14 +11,15 @@ namespace mhr {
 
 constexpr int kMidThreads = 1024;               // middle-join block (one per SM)
 constexpr int kMidWarps = kMidThreads / 32;
-constexpr int kMaxChunk = 16384;                // edges per work item, upper limit
+constexpr int kMaxChunk = 32768;                // edges per work item, upper limit (<= 32 x threads)
 constexpr int kDefaultChunk = 16384;
+static_assert(kMaxChunk / 32 <= kMidThreads, "one 32-edge group per thread in the group map");
 constexpr int kCandCap = 4096;                  // per-CTA fp32 candidate buffer
 constexpr int kDenseLimit = kCandCap / 2;       // band denser than this -> exact path
 constexpr int kMaxBmWords = 32768;              // shared-memory bitmap: 2^20 vertices
 constexpr int kRankWords = 8;                   // one rank entry per 256 bitmap bits
 constexpr int kMaxRank = kMaxBmWords / kRankWords;
-constexpr int kUnroll = 8;                      // 32-edge groups in flight per warp
+constexpr int kDefaultTile = 4;                 // 32-edge groups in flight per warp (also 8)
 
 // fp32 candidate: one path, identified by its hop-1 entry (index into the CSR
 // row of s), its hop-3 entry (index into the reverse CSR row of t) and r2.
@@ -107,6 +108,9 @@ struct PlanDev {
     uint32_t* hist;     // [nq * 256] bucket counts
     int64_t* hscan;     // [nq * 256 + 1]
     uint32_t* item_ub;  // [item_cap] key of the largest row bound in a work item
+    uint4* item_desc;   // [item_cap] (query | seeded << 31, near entry holding the item's first
+                        //  edge, near entry holding its last edge, index of the item in its query)
+    uint2* seed_k;      // [nq] near entries holding edge kSeedEdges - 1 and edge kSeedEdges
     // per query [nq] (+1 for item_off)
     int32_t* status;
     int32_t* dir;       // 1 = forward (scan out-rows of hop-1 vertices), 0 = backward
@@ -129,6 +133,7 @@ struct PlanDev {
     int32_t* n_out;     // [nq]
     unsigned long long* counters;  // kCntCount
     unsigned long long* cursors;   // [grid] next item of each CTA's own range
+    uint32_t* drained;             // [(grid + 31) / 32] bit v: range v has no item left
     int64_t* partials;             // scan scratch
 };
 

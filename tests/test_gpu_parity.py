@@ -180,7 +180,7 @@ def test_topk_dyadic_many_ties_large_K(mhr):
 
 
 @pytest.mark.parametrize("prune,order", [(0, 0), (1, 0), (1, 1)])
-@pytest.mark.parametrize("chunk", [32, 64, 1024, 16384])
+@pytest.mark.parametrize("chunk", [32, 64, 1024, 16384, 32768])
 def test_topk_chunk_sizes(mhr, chunk, prune, order):
     """Work items of any size give the same answer (several items per query,
     ragged tails, hub rows split across items)."""
@@ -390,4 +390,34 @@ def test_tensor_core_screen_rejects_unsupported(mhr):
     G = mhr.load_kg(g, score_fn="distmult")
     with pytest.raises(mhr.MhrError):
         mhr.mhr_topk_paths(G, 0, 1, 5, opts={"precision": 1})
+    G.close()
+
+
+def test_autotune_picks_a_candidate_and_keeps_results(mhr):
+    """The launch-shape autotuner times every (work-item size, scan tile) pair
+    on the batch and returns the fastest; results with the chosen shape equal
+    the default's and the oracle's."""
+    g = synth.gen_rmat_kg(14, 12000, 200_000, 6, 3, seed=41)
+    g.vemb, g.remb = synth.gen_embeddings(g.n, g.R, 32, 1 / 8, seed=41)
+    S, T = synth.queries_edge_biased(g, 24, seed=41)
+    G = mhr.load_kg(g)
+    opts = {"prune": 1, "order": 1}
+    chunks, tiles = (64, 512, 2048), (4, 8)
+    bc, bt, ms = mhr.mhr_autotune(G, S, T, 30, opts=opts, chunks=chunks, tiles=tiles, reps=2)
+    assert bc in chunks and bt in tiles and set(ms) == {(c, t) for c in chunks for t in tiles}
+    assert all(v > 0 for v in ms.values()) and ms[(bc, bt)] == min(ms.values())
+    out_b, n_b = mhr.mhr_topk_paths_batched(G, S, T, 30, opts={**opts, "chunk": bc, "tile": bt})
+    out_d, n_d = mhr.mhr_topk_paths_batched(G, S, T, 30)
+    assert np.array_equal(n_b, n_d)
+    for q in range(len(S)):
+        assert out_b[q][: n_b[q]].tobytes() == out_d[q][: n_d[q]].tobytes()
+    want, n_want = oracle.topk_paths_batch(g, S, T, 30)
+    for q in range(len(S)):
+        compare_query(out_b[q], n_b[q], want[q][: n_want[q]], ctx=q)
+    with pytest.raises(mhr.MhrError):
+        mhr.mhr_autotune(G, S, T, 30, chunks=(100,))
+    with pytest.raises(mhr.MhrError):
+        mhr.mhr_autotune(G, S, T, 30, tiles=(5,))
+    with pytest.raises(mhr.MhrError):
+        mhr.mhr_topk_paths_batched(G, S, T, 30, opts={"tile": 6})
     G.close()
