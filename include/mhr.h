@@ -117,7 +117,7 @@ typedef struct {
 /* Query options; a NULL pointer means all defaults (zeros). */
 typedef struct {
     int32_t chunk;       /* edges per work item of the middle join: 0 = default (16384), else a
-                            multiple of 32 in [32, 32768] (MHR_EINVAL otherwise) */
+                            multiple of 32 in [32, 16384] (MHR_EINVAL otherwise) */
     int32_t order;       /* order of intermediate vertices: 0 natural, 1 by score
                             bound, 2 by the learned score of `mlp` */
     int32_t prune;       /* 1 = skip work items, rows and middle edges whose provable
@@ -195,8 +195,8 @@ mhr_status mhr_topk_paths_batched(const mhr_graph* g, int32_t nq, const uint32_t
  * counterpart; its OpenMP loops have no tunable shape).  Runs
  * mhr_topk_paths_batched on the nq queries (s, t; mem applies to both) with
  * opts and every pair (chunks[i], tiles[j]) as (opts->chunk, opts->tile):
- * chunks are multiples of 32 in [32, 32768] (NULL: {4096, 8192, 16384, 32768},
- * n_chunks = 4), tiles are 4 or 8 (NULL: {4, 8}, n_tiles = 2).  Each pair gets
+ * chunks are multiples of 32 in [32, 16384] (NULL: {4096, 8192, 16384},
+ * n_chunks = 3), tiles are 4 or 8 (NULL: {4, 8}, n_tiles = 2).  Each pair gets
  * one untimed run, then reps timed runs, timed by CUDA events around the
  * launch sequence on cuda_stream; ms_out[i * n_tiles + j] (optional, host) =
  * the fastest of the pair's runs; *best_chunk and *best_tile (host) = the pair

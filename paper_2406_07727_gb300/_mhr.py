@@ -333,7 +333,7 @@ def mhr_topk_paths_batched(g: Graph, S, T, K: int, out=None, n_out=None, opts=No
     return out, n_out
 
 
-def mhr_autotune(g: Graph, S, T, K: int, opts=None, chunks=(4096, 8192, 16384, 32768), tiles=(4, 8),
+def mhr_autotune(g: Graph, S, T, K: int, opts=None, chunks=(4096, 8192, 16384), tiles=(4, 8),
                  reps: int = 3, stream=None):
     """Time the batched search on (S, T) for every (work-item size, scan tile)
     pair; returns (best chunk, best tile, {(chunk, tile): ms})."""

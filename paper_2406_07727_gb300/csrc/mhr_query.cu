@@ -285,10 +285,13 @@ __global__ void k_lists(const PlanDev* __restrict__ P, DevGraph g) {
             if (sideA) {
                 e.deg = static_cast<uint32_t>(g.off[vtx + 1] - g.off[vtx]);
                 e.rowstart = static_cast<uint32_t>(g.off[vtx]);
+                e.midw = g.maxw_out[vtx];
             } else {
                 e.deg = static_cast<uint32_t>(g.roff[vtx + 1] - g.roff[vtx]);
                 e.rowstart = static_cast<uint32_t>(g.roff[vtx]);
+                e.midw = g.maxw_in[vtx];
             }
+            e.pad = 0u;
             P->list[base + j] = e;
             P->degv[base + j] = e.deg;
             qkey = 2u * static_cast<uint32_t>(q) + (sideA ? 0u : 1u);
@@ -476,6 +479,8 @@ __global__ void k_order_perm(const PlanDev* __restrict__ P) {
     }
 }
 
+constexpr uint32_t kGposMulti = 0xffffffffu;   // group spans several near rows
+constexpr uint32_t kGposPruned = 0xfffffffeu;  // group inside one row whose bound misses the band
 constexpr int kSeedEdges = 2048;    // edges of each query's highest-bound rows done by the seed launch
 constexpr int kSeedMinItems = 2;    // queries with fewer work items are not seeded
 
@@ -494,6 +499,7 @@ __global__ void k_near(const PlanDev* __restrict__ P, DevGraph g) {
         const ListEnt e = P->list[old];
         const int64_t pre = P->scan4[x] - P->scan4[base];
         P->nearP[x] = make_uint2(static_cast<uint32_t>(pre), e.rowstart);
+        P->nearL[x] = e;
         const float b = P->bnat[old];
         P->nearB[x] = b;
         if (e.deg == 0) continue;
@@ -533,6 +539,7 @@ struct MidSmem {
     uint32_t rank[kMaxRank + 8];
     Cand cand[kCandCap];
     uint32_t gmap[kMaxChunk / 32 + 32];
+    uint32_t gpos[kMaxChunk / 32];  // CSR position of a single-row group's first edge, or a marker
     uint32_t hist[256];
     uint32_t bc[4];
     int64_t red[33];
@@ -556,6 +563,9 @@ struct MidSmem {
     int64_t total_items;
     uint32_t f_gk;  // the query's shared K-th score key as read when the item was taken
     unsigned long long c_scanned, c_hits, c_cands, c_skipped;
+#ifdef MHR_PHASE_TIMING
+    unsigned long long sub[kMidWarps][6];  // per-warp cycles of the sub-phases (timing builds)
+#endif
 };
 
 // block-wide in-place compaction of the candidate buffer to s32 >= thr
@@ -899,6 +909,15 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
 #define MHR_WSTART() (t_w = clock64())
 #define MHR_WEND(acc) ((acc) += clock64() - t_w)
 #define MHR_COUNT(c) (++(c))
+    unsigned long long t_sub = 0;
+    for (int i = threadIdx.x; i < kMidWarps * 6; i += blockDim.x) (&sm.sub[0][0])[i] = 0ull;
+#define MHR_SUB_START() (t_sub = clock64())
+#define MHR_SUB(i)                                               \
+    do {                                                         \
+        const unsigned long long now__ = clock64();              \
+        if (lane == 0) sm.sub[warp][i] += now__ - t_sub;        \
+        t_sub = now__;                                           \
+    } while (0)
 #else
 #define MHR_PHASE(i) \
     do {             \
@@ -906,6 +925,8 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
 #define MHR_WSTART() ((void)0)
 #define MHR_WEND(acc) ((void)0)
 #define MHR_COUNT(c) ((void)0)
+#define MHR_SUB_START() ((void)0)
+#define MHR_SUB(i) ((void)0)
 #endif
     int cur_q = -1;
     int victim = 0;  // thread 0: offset of the range it currently drains
@@ -1029,7 +1050,9 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         const int ngroups = static_cast<int>((e1 - e0 + 31) / 32);
         const int near_cnt = sm.near_cnt;
         const uint2* nearP = P->nearP + sm.near_base;
+        const float* nearB = P->nearB + sm.near_base;
         const uint32_t s_near32 = static_cast<uint32_t>(sm.s_near);
+        const float thr_scan = sm.thr_keep;
         // --- group -> owning near entry (+1), by marking group starts then a prefix max
         for (int i = threadIdx.x; i < ngroups; i += blockDim.x) sm.gmap[i] = 0u;
         __syncthreads();
@@ -1062,7 +1085,22 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
             }
             __syncthreads();
             if (warp > 0) v = max(v, sm.redu[warp - 1]);
-            if (threadIdx.x < ngroups) sm.gmap[threadIdx.x] = v;
+            if (threadIdx.x < ngroups) {
+                sm.gmap[threadIdx.x] = v;
+                // a group inside one near row: CSR position of its first edge, or
+                // the whole group pruned by the row bound
+                const uint32_t kk = v - 1u;
+                const uint32_t gs = e0 + 32u * threadIdx.x;
+                const uint32_t ge = min(gs + 32u, e1);
+                const uint2 pk = nearP[kk];
+                const uint32_t nxt = (kk + 1u < static_cast<uint32_t>(near_cnt)) ? nearP[kk + 1u].x : s_near32;
+                uint32_t gp = kGposMulti;
+                if (ge <= nxt) {
+                    gp = pk.y + (gs - pk.x);
+                    if (prune && __fadd_ru(nearB[kk], slack) < thr_scan) gp = kGposPruned;
+                }
+                sm.gpos[threadIdx.x] = gp;
+            }
         }
         __syncthreads();
 
@@ -1071,23 +1109,25 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         const uint32_t* colsrc = sm.dir ? g.col : g.rcol;
         const ListEnt* far = P->list + sm.far_base;
         const int far_cnt = sm.far_cnt;
-        const float* nearB = P->nearB + sm.near_base;
-        const float thr_scan = sm.thr_keep;
         MHR_WSTART();
         for (int gb = warp * UNROLL; gb < ngroups; gb += kMidWarps * UNROLL) {
+            MHR_SUB_START();
             uint2 ne[UNROLL];
-            uint32_t kk[UNROLL];
+            uint32_t kk[UNROLL], gp[UNROLL];
             float rb[UNROLL];
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
                 const int gidx = gb + u;
                 ne[u] = make_uint2(s_near32, 0u);
                 kk[u] = 0;
+                gp[u] = kGposPruned;
                 rb[u] = 0.f;
                 if (gidx < ngroups) {
                     kk[u] = sm.gmap[gidx] - 1u;
+                    gp[u] = sm.gpos[gidx];
                     const uint32_t idx = kk[u] + lane;
-                    if (idx < static_cast<uint32_t>(near_cnt)) {
+                    // rows of a group spanning several near rows: 32 row starts from kk on
+                    if (gp[u] == kGposMulti && idx < static_cast<uint32_t>(near_cnt)) {
                         ne[u] = nearP[idx];
                         if (prune) rb[u] = nearB[idx];
                     }
@@ -1105,25 +1145,36 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                 if (gidx < ngroups) {
                     const uint32_t gs = e0 + 32u * gidx;
                     const uint32_t e = gs + lane;
-                    const uint32_t pos = ne[u].x - gs;
-                    const uint32_t bit = (lane >= 1 && pos >= 1 && pos <= 31) ? (1u << pos) : 0u;
-                    const uint32_t mask = __reduce_or_sync(FULL, bit);
-                    const int c = __popc(mask & lanemask_le());
-                    const uint32_t pm = __shfl_sync(FULL, ne[u].x, c);
-                    const uint32_t rs = __shfl_sync(FULL, ne[u].y, c);
                     valid[u] = e < e1;
-                    if (prune) {
-                        // no path through this row can reach the kept band: skip its edges
-                        const float rowb = __fadd_ru(__shfl_sync(FULL, rb[u], c), slack);
-                        if (valid[u] && rowb < thr_scan) {
-                            valid[u] = false;
-                            ++n_pruned;
+                    if (gp[u] == kGposMulti) {  // warp-uniform
+                        // lane -> its row: count the row starts in (gs, e]
+                        const uint32_t pos = ne[u].x - gs;
+                        const uint32_t bit = (lane >= 1 && pos >= 1 && pos <= 31) ? (1u << pos) : 0u;
+                        const uint32_t mask = __reduce_or_sync(FULL, bit);
+                        const int c = __popc(mask & lanemask_le());
+                        const uint32_t pm = __shfl_sync(FULL, ne[u].x, c);
+                        const uint32_t rs = __shfl_sync(FULL, ne[u].y, c);
+                        if (prune) {
+                            // no path through this row can reach the kept band: skip its edges
+                            const float rowb = __fadd_ru(__shfl_sync(FULL, rb[u], c), slack);
+                            if (valid[u] && rowb < thr_scan) {
+                                valid[u] = false;
+                                ++n_pruned;
+                            }
                         }
+                        epos[u] = rs + (e - pm);
+                        nk[u] = kk[u] + c;
+                    } else if (gp[u] == kGposPruned) {
+                        if (valid[u]) ++n_pruned;
+                        valid[u] = false;
+                        nk[u] = kk[u];
+                    } else {
+                        epos[u] = gp[u] + lane;
+                        nk[u] = kk[u];
                     }
-                    epos[u] = rs + (e - pm);
-                    nk[u] = kk[u] + c;
                 }
             }
+            MHR_SUB(0);
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u)
                 if (valid[u]) xv[u] = __ldg(colsrc + epos[u]);
@@ -1173,6 +1224,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                     }
                 }
             }
+            MHR_SUB(1);
         }
         MHR_WEND(wt_scan);
         if (threadIdx.x == 0) sm.round_cnt = sm.cand_cnt;
@@ -1189,8 +1241,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         // entries, then groups of G lanes score H = 32 / G hits at a time over
         // G rounds, so every warp keeps H hits' embedding rows in flight.
         const uint16_t* relsrc = sm.dir ? g.rel : g.rrel;
-        const ListEnt* nearL = P->list + sm.near_base;
-        const uint32_t* nperm = P->nperm + sm.near_base;
+        const ListEnt* nearL = P->nearL + sm.near_base;  // ordered position
         const float* w1s = P->w32 + sm.a_base;
         const float* w3s = P->w32 + sm.c_base;
         const int G = P->score_width, H = 32 / G;
@@ -1214,6 +1265,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                     if (!loaded) {
                         const int hb = b * 32;
                         if (hb >= nh) break;
+                        MHR_SUB_START();
                         const int hi = hb + lane;
                         const bool live = hi < nh;
                         float mw1 = 0.f, mw3 = 0.f;
@@ -1223,7 +1275,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                         if (live) {
                             const Hit ht = hits[hi];
                             hnk = ht.near_k;
-                            const ListEnt ne = nearL[nperm[ht.near_k]];
+                            const ListEnt ne = nearL[ht.near_k];
                             const ListEnt fe = far[ht.far_k];
                             const ListEnt& ea = sm.dir ? ne : fe;  // hop-1 side (u)
                             const ListEnt& ec = sm.dir ? fe : ne;  // hop-3 side (v)
@@ -1240,7 +1292,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                             alive = true;
                             if (prune) {
                                 // w2 <= the largest weight of any out-edge of u and of any in-edge of v
-                                const float mw2 = fminf(g.maxw_out[hu], g.maxw_in[hv]);
+                                const float mw2 = fminf(ea.midw, ec.midw);
                                 if (__fadd_ru(__fadd_rn(__fadd_rn(mw1, mw2), mw3), slack) < thr) {
                                     alive = false;
                                     ++n_pruned;
@@ -1248,6 +1300,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                             }
                         }
                         // move the surviving hits to the low lanes
+                        MHR_SUB(2);
                         const unsigned am = __ballot_sync(FULL, alive);
                         const int nsurv = __popc(am);
                         if (prune) {
@@ -1288,6 +1341,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                             if (lane / H == r) w2m = tw;
                         }
                         hw2 = w2m;
+                        MHR_SUB(3);
                         const float smax = __fadd_rn(__fadd_rn(mw1, hw2), mw3);
                         // training labels (plain runs only): best path score through the near entry
                         if (P->label && live2) atomicMax(&P->ubest[sm.near_base + hnk], f2key(smax));
@@ -1365,6 +1419,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                         if (mine) slice += c0 > excl ? min(c0 - excl, rem) : 0u;
                         pend = __ballot_sync(FULL, mine && slice < ncomb);
                     }
+                    MHR_SUB(4);
                     if (stop) {
                         done = false;
                         break;
@@ -1398,6 +1453,14 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
             atomicAdd(&wr[3], wt_score);
         }
         __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long a[6] = {0, 0, 0, 0, 0, 0};
+            for (int w = 0; w < kMidWarps; ++w)
+                for (int i = 0; i < 6; ++i) a[i] += sm.sub[w][i];
+            printf("MHR_SUB %d %d nearP %llu col_bitmap_hits %llu hit_load %llu w2 %llu combos %llu\n", blockIdx.x,
+                   SEED ? 1 : 0, a[0] / kMidWarps, a[1] / kMidWarps, a[2] / kMidWarps, a[3] / kMidWarps,
+                   a[4] / kMidWarps);
+        }
         if (threadIdx.x == 0)
             printf("MHR_WARPS %d %d items %llu iters %llu probes %llu switches %llu scan_max %llu scan_mean %llu "
                    "score_max %llu score_mean %llu\n",
@@ -1472,15 +1535,15 @@ __global__ void __launch_bounds__(1024) k_merge1(const PlanDev* __restrict__ P) 
     }
 }
 
-// fp64 rescoring of the band.  The canonical order fixes only the
-// accumulation acc = acc + y_j (j ascending); the terms y_j = |(a_j + b_j) - c_j|
-// (or (a_j * b_j) * c_j) are independent.  A warp takes up to ten candidates
-// (thirty edge sums): all lanes compute terms into shared memory, then lane e
-// runs the sequential fp64 sum of edge e, so the sums of thirty edges share one
-// stream of warp instructions.
+// fp64 rescoring of the band.  The canonical order fixes the accumulation
+// acc = acc + y_j (j ascending) of each edge; the terms y_j = |(a_j + b_j) - c_j|
+// (or (a_j * b_j) * c_j) are formed from the stored values converted exactly.
+// A warp takes up to ten candidates: lane 3c + e (e = 0, 1, 2) runs the
+// sequential sum of edge e of candidate c straight from the three embedding
+// rows (16-byte loads, several in flight), so thirty independent chains share
+// the warp.
 constexpr int kRsWarps = 8;
 constexpr int kRsCands = 10;
-constexpr int kRsChunk = 32;
 
 __device__ __forceinline__ double term64(const DevGraph& g, uint32_t h, uint32_t r, uint32_t t, int j) {
     const double a = emb_f64(g.vemb, g.dtype, h, g.d, j);
@@ -1490,9 +1553,40 @@ __device__ __forceinline__ double term64(const DevGraph& g, uint32_t h, uint32_t
     return __dmul_rn(__dmul_rn(a, b), c);
 }
 
+__device__ __forceinline__ double acc4(double acc, const float4& a, const float4& b, const float4& c, bool transe) {
+    if (transe) {
+        acc = __dadd_rn(acc, fabs(__dsub_rn(__dadd_rn(static_cast<double>(a.x), static_cast<double>(b.x)), static_cast<double>(c.x))));
+        acc = __dadd_rn(acc, fabs(__dsub_rn(__dadd_rn(static_cast<double>(a.y), static_cast<double>(b.y)), static_cast<double>(c.y))));
+        acc = __dadd_rn(acc, fabs(__dsub_rn(__dadd_rn(static_cast<double>(a.z), static_cast<double>(b.z)), static_cast<double>(c.z))));
+        acc = __dadd_rn(acc, fabs(__dsub_rn(__dadd_rn(static_cast<double>(a.w), static_cast<double>(b.w)), static_cast<double>(c.w))));
+    } else {
+        acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(static_cast<double>(a.x), static_cast<double>(b.x)), static_cast<double>(c.x)));
+        acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(static_cast<double>(a.y), static_cast<double>(b.y)), static_cast<double>(c.y)));
+        acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(static_cast<double>(a.z), static_cast<double>(b.z)), static_cast<double>(c.z)));
+        acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(static_cast<double>(a.w), static_cast<double>(b.w)), static_cast<double>(c.w)));
+    }
+    return acc;
+}
+
+// fp64 weight of edge (h, r, t) in the canonical order
+__device__ __forceinline__ double edge_w64_seq(const DevGraph& g, uint32_t h, uint32_t r, uint32_t t) {
+    const int d = g.d;
+    const bool transe = g.fn == MHR_SCORE_TRANSE_L1;
+    double acc = 0.0;
+    if (g.dtype == MHR_F32 && (d & 3) == 0) {
+        const float4* A = reinterpret_cast<const float4*>(static_cast<const float*>(g.vemb) + static_cast<int64_t>(h) * d);
+        const float4* B = reinterpret_cast<const float4*>(static_cast<const float*>(g.remb) + static_cast<int64_t>(r) * d);
+        const float4* C = reinterpret_cast<const float4*>(static_cast<const float*>(g.vemb) + static_cast<int64_t>(t) * d);
+        const int n4 = d >> 2;
+#pragma unroll 4
+        for (int j = 0; j < n4; ++j) acc = acc4(acc, __ldg(A + j), __ldg(B + j), __ldg(C + j), transe);
+    } else {
+        for (int j = 0; j < d; ++j) acc = __dadd_rn(acc, term64(g, h, r, t, j));
+    }
+    return transe ? __dsub_rn(g.gamma, acc) : acc;
+}
+
 __global__ void __launch_bounds__(kRsWarps * 32) k_rescore(const PlanDev* __restrict__ P, DevGraph g) {
-    __shared__ double ys[kRsWarps][3 * kRsCands][kRsChunk + 1];
-    __shared__ uint32_t eh[kRsWarps][3 * kRsCands], er[kRsWarps][3 * kRsCands], et[kRsWarps][3 * kRsCands];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nq = P->nq, cap = P->band_cap;
     const int64_t gw = blockIdx.x * static_cast<int64_t>(kRsWarps) + w;
@@ -1507,43 +1601,30 @@ __global__ void __launch_bounds__(kRsWarps * 32) k_rescore(const PlanDev* __rest
         const int nc = min(kRsCands, nb - i0);
         const int64_t x0 = static_cast<int64_t>(q) * cap + i0;
         const uint32_t s = P->S[q], t = P->T[q];
-        mhr_path p;  // lane c < nc: candidate c
-        if (lane < nc) {
-            const Cand c = P->band_cand[x0 + lane];
-            const int64_t p1 = g.off[s] + c.a_idx;
-            const int64_t p3 = g.roff[t] + c.c_idx;
+        const int c = lane / 3, e = lane - 3 * (lane / 3);  // candidate, edge
+        double we = 0.0;
+        mhr_path p;
+        if (c < nc) {
+            const Cand cd = P->band_cand[x0 + c];
+            const int64_t p1 = g.off[s] + cd.a_idx;
+            const int64_t p3 = g.roff[t] + cd.c_idx;
             p.u = g.col[p1];
             p.r1 = g.rel[p1];
             p.v = g.rcol[p3];
             p.r3 = g.rrel[p3];
-            p.r2 = c.r2;
+            p.r2 = cd.r2;
             p.pad = 0;
-            eh[w][3 * lane] = s;    er[w][3 * lane] = p.r1;     et[w][3 * lane] = p.u;
-            eh[w][3 * lane + 1] = p.u; er[w][3 * lane + 1] = p.r2; et[w][3 * lane + 1] = p.v;
-            eh[w][3 * lane + 2] = p.v; er[w][3 * lane + 2] = p.r3; et[w][3 * lane + 2] = t;
+            const uint32_t h = e == 0 ? s : (e == 1 ? p.u : p.v);
+            const uint32_t r = e == 0 ? p.r1 : (e == 1 ? p.r2 : p.r3);
+            const uint32_t tt = e == 0 ? p.u : (e == 1 ? p.v : t);
+            we = edge_w64_seq(g, h, r, tt);
         }
-        __syncwarp();
-        const int ne = 3 * nc;
-        double acc = 0.0;  // lane e < ne: sum of edge e
-        for (int c0 = 0; c0 < g.d; c0 += kRsChunk) {
-            const int n = min(kRsChunk, g.d - c0);
-            for (int k = lane; k < ne * n; k += 32) {
-                const int e = k / n, j = k - e * n;
-                ys[w][e][j] = term64(g, eh[w][e], er[w][e], et[w][e], c0 + j);
-            }
-            __syncwarp();
-            if (lane < ne)
-                for (int j = 0; j < n; ++j) acc = __dadd_rn(acc, ys[w][lane][j]);
-            __syncwarp();
-        }
-        const double we = (g.fn == MHR_SCORE_TRANSE_L1) ? __dsub_rn(g.gamma, acc) : acc;
-        const int b = 3 * (lane < nc ? lane : 0);
+        const int b = 3 * (c < nc ? c : 0);
         const double w1 = __shfl_sync(FULL, we, b), w2 = __shfl_sync(FULL, we, b + 1), w3 = __shfl_sync(FULL, we, b + 2);
-        if (lane < nc) {
+        if (c < nc && e == 0) {
             p.score = __dadd_rn(__dadd_rn(w1, w2), w3);
-            P->band_path[x0 + lane] = p;
+            P->band_path[x0 + c] = p;
         }
-        __syncwarp();
     }
 }
 
@@ -1848,8 +1929,8 @@ static size_t merge2_smem_bytes(int band_cap) {
 static mhr_status ensure_slots(Plan* p, int64_t X) {
     if (X <= p->slot_cap && p->slot_mem) return MHR_OK;
     int64_t cap = std::max<int64_t>(X, std::max<int64_t>(p->slot_cap * 2, 1 << 16));
-    // per slot: w32 4, flag 4, degv 4, scan1 8, scan2 8, list 24, nearP 8, nearB 4,
-    // okey 4, orank 4, bnat 4, nperm 4, degv3 4, scan4 8, mlp_pred 4
+    // per slot: w32 4, flag 4, degv 4, scan1 8, scan2 8, list 32, nearP 8, nearL 32, nearB 4,
+    // okey 4, orank 4, bnat 4, nperm 4, degv3 4, scan4 8, mlp_pred 4, ubest 4
     const size_t a8 = 256;
     size_t o = 0;
     const size_t o_w32 = o; o = align_up(o + 4 * cap, a8);
@@ -1859,6 +1940,7 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
     const size_t o_s2 = o; o = align_up(o + 8 * (cap + 1), a8);
     const size_t o_list = o; o = align_up(o + sizeof(ListEnt) * cap, a8);
     const size_t o_near = o; o = align_up(o + sizeof(uint2) * cap, a8);
+    const size_t o_nearl = o; o = align_up(o + sizeof(ListEnt) * cap, a8);
     const size_t o_nb = o; o = align_up(o + sizeof(float) * cap, a8);
     const size_t o_okey = o; o = align_up(o + 4 * cap, a8);
     const size_t o_orank = o; o = align_up(o + 4 * cap, a8);
@@ -1885,6 +1967,7 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
     p->h.scan2 = reinterpret_cast<int64_t*>(b + o_s2);
     p->h.list = reinterpret_cast<ListEnt*>(b + o_list);
     p->h.nearP = reinterpret_cast<uint2*>(b + o_near);
+    p->h.nearL = reinterpret_cast<ListEnt*>(b + o_nearl);
     p->h.nearB = reinterpret_cast<float*>(b + o_nb);
     p->h.okey = reinterpret_cast<uint32_t*>(b + o_okey);
     p->h.orank = reinterpret_cast<uint32_t*>(b + o_orank);
@@ -2151,7 +2234,7 @@ static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint
                             const mhr_query_opts* opts, cudaStream_t st, Plan** plan_out, bool label = false) {
     int chunk = (opts && opts->chunk > 0) ? opts->chunk : kDefaultChunk;
     if (chunk > kMaxChunk || chunk < 32 || (chunk & 31))
-        return fail(MHR_EINVAL, "opts->chunk must be a multiple of 32 in [32, 32768]");
+        return fail(MHR_EINVAL, "opts->chunk must be a multiple of 32 in [32, 16384]");
     const int precision = opts ? opts->precision : 0;
     if (precision != 0 && precision != 1) return fail(MHR_EINVAL, "opts->precision must be 0 or 1");
     const int tile = (opts && opts->tile) ? opts->tile : kDefaultTile;
@@ -2296,11 +2379,11 @@ extern "C" mhr_status mhr_autotune(const mhr_graph* gc, int32_t nq, const uint32
                                    int32_t* best_tile, float* ms_out, void* cuda_stream) {
     MHR_TRY(check_graph(gc));
     mhr_graph* G = const_cast<mhr_graph*>(gc);
-    static const int32_t kChunks[4] = {4096, 8192, 16384, 32768};
+    static const int32_t kChunks[3] = {4096, 8192, 16384};
     static const int32_t kTiles[2] = {4, 8};
     if (!chunks) {
         chunks = kChunks;
-        n_chunks = 4;
+        n_chunks = 3;
     }
     if (!tiles) {
         tiles = kTiles;
@@ -2313,7 +2396,7 @@ extern "C" mhr_status mhr_autotune(const mhr_graph* gc, int32_t nq, const uint32
     if (mem != MHR_MEM_HOST && mem != MHR_MEM_DEVICE) return fail(MHR_EINVAL, "unknown mem kind");
     for (int i = 0; i < n_chunks; ++i)
         if (chunks[i] > kMaxChunk || chunks[i] < 32 || (chunks[i] & 31))
-            return fail(MHR_EINVAL, "chunk candidates must be multiples of 32 in [32, 32768]");
+            return fail(MHR_EINVAL, "chunk candidates must be multiples of 32 in [32, 16384]");
     for (int i = 0; i < n_tiles; ++i)
         if (tiles[i] != 4 && tiles[i] != 8) return fail(MHR_EINVAL, "tile candidates must be 4 or 8");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

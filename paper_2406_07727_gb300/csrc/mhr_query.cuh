@@ -11,7 +11,7 @@ namespace mhr {
 
 constexpr int kMidThreads = 1024;               // middle-join block (one per SM)
 constexpr int kMidWarps = kMidThreads / 32;
-constexpr int kMaxChunk = 32768;                // edges per work item, upper limit (<= 32 x threads)
+constexpr int kMaxChunk = 16384;                // edges per work item, upper limit (<= 32 x threads)
 constexpr int kDefaultChunk = 16384;
 static_assert(kMaxChunk / 32 <= kMidThreads, "one 32-edge group per thread in the group map");
 constexpr int kCandCap = 4096;                  // per-CTA fp32 candidate buffer
@@ -47,8 +47,11 @@ struct ListEnt {
     float maxw;          // max fp32 weight over the run
     uint32_t deg;        // scan degree: out-degree (hop-1 side) / in-degree (hop-3 side)
     uint32_t rowstart;   // first CSR (or reverse CSR) position of that scan row
+    float midw;          // bound of any middle-edge weight at this vertex: the largest fp32
+                         // weight of its out-edges (hop-1 side) / in-edges (hop-3 side)
+    uint32_t pad;
 };
-static_assert(sizeof(ListEnt) == 24, "ListEnt is 24 bytes");
+static_assert(sizeof(ListEnt) == 32, "ListEnt is 32 bytes");
 
 enum {
     kCntItem = 0,
@@ -94,6 +97,7 @@ struct PlanDev {
     uint32_t* degv;
     int64_t* scan2;
     uint2* nearP;  // (prefix of scan degree within the query, row start)
+    ListEnt* nearL;  // near entries in ordered position
     float* nearB;  // upper bound of the fp32 score of any path through a near entry
     // near-row ordering (slot arrays [X], scans [X+1])
     uint32_t* okey;     // order key of a near entry (natural position)
