@@ -441,7 +441,8 @@ mhr_status load_impl(const mhr_graph_desc* desc, mhr_graph* g, cudaStream_t st) 
         int64_t *n_dev, *partials;
         MHR_CUDA_TRY(tmp.alloc(&indeg, sizeof(uint32_t) * n));
         MHR_CUDA_TRY(tmp.alloc(&n_dev, sizeof(int64_t)));
-        MHR_CUDA_TRY(tmp.alloc(&partials, sizeof(int64_t) * (kScanGrid + 1)));
+        MHR_CUDA_TRY(tmp.alloc(&partials, sizeof(int64_t) * kScanPartials));
+        MHR_CUDA_TRY(cudaMemsetAsync(partials, 0, sizeof(int64_t) * kScanPartials, st));
         MHR_CUDA_TRY(cudaMemsetAsync(indeg, 0, sizeof(uint32_t) * n, st));
         MHR_CUDA_TRY(cudaMemcpyAsync(n_dev, &n, sizeof(int64_t), cudaMemcpyHostToDevice, st));
         if (E) k_count_in<<<grid, 256, 0, st>>>(col, E, indeg);

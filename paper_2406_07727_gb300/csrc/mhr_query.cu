@@ -534,6 +534,15 @@ __global__ void k_near(const PlanDev* __restrict__ P, DevGraph g) {
 // the middle join (persistent)
 // ===========================================================================
 constexpr int kRelCacheVecs = 512;  // 8 KB of fp32 relation embeddings
+// a work item taken from the queue, ready to run
+struct ItemSel {
+    int64_t item;  // == total items: none left
+    int32_t q;
+    uint32_t e0, e1, k0, k1;  // edge range; near entries holding its first and last edge
+    uint32_t gk;              // the query's shared K-th score key when it was taken
+    uint32_t ub;              // key of the item's largest row bound
+};
+
 struct MidSmem {
     uint32_t bm[kMaxBmWords];
     uint32_t rank[kMaxRank + 8];
@@ -562,6 +571,9 @@ struct MidSmem {
     double two_err;
     int64_t total_items;
     uint32_t f_gk;  // the query's shared K-th score key as read when the item was taken
+    ItemSel nx;     // next item, taken during the current item's score phase
+    int nx_ready;
+    int victim;     // offset of the range the CTA currently drains
     unsigned long long c_scanned, c_hits, c_cands, c_skipped;
 #ifdef MHR_PHASE_TIMING
     unsigned long long sub[kMidWarps][6];  // per-warp cycles of the sub-phases (timing builds)
@@ -874,6 +886,81 @@ __device__ __forceinline__ int64_t take_item(const PlanDev* __restrict__ P, int6
     return total_items;
 }
 
+// Takes the next work item that cannot be skipped and prepares it.  An item is
+// skipped without touching the CTA's query state when its query is being
+// recomputed exactly, when the seed launch did all of it, or when no row of it
+// can reach the query's kept band.  Run by one thread at a time.
+template <bool SEED>
+__device__ void select_item(MidSmem& sm, const PlanDev* __restrict__ P, int nq, bool prune, ItemSel& out,
+                            unsigned long long& iters, unsigned long long& probes) {
+    const int64_t total_items = sm.total_items;
+    out.item = total_items;
+    out.q = -1;
+    for (;;) {
+        ++iters;
+        int64_t it = total_items;
+        if (SEED) {
+            // one item per seeded query: its first one
+            if (prune) {
+                for (;;) {
+                    const int qq = static_cast<int>(atomicAdd(&P->counters[kCntSeed], 1ull));
+                    if (qq >= nq) break;
+                    if (seeded_query(P, qq, prune)) {
+                        it = P->item_off[qq];
+                        break;
+                    }
+                }
+            }
+        } else {
+            it = take_item(P, total_items, sm.victim, probes);
+        }
+        if (it >= total_items) return;
+        const uint4 dsc = P->item_desc[it];
+        const uint32_t ub = P->item_ub[it];
+        const int iq = static_cast<int>(dsc.x & 0x7fffffffu);
+        const bool seeded = (dsc.x >> 31) != 0u;
+        const int64_t li = dsc.w;
+        const int dense = __ldcg(P->dense + iq);
+        uint32_t gk = __ldcg(P->thr_g + iq);
+        const int64_t s_near = P->s_near[iq];
+        const uint32_t lt = *reinterpret_cast<volatile uint32_t*>(&sm.lt_key);
+        if (iq == *reinterpret_cast<volatile int*>(&sm.q) && lt > gk) gk = lt;
+        const int64_t chunk = P->chunk;
+        const int64_t first = min(chunk, s_near);  // edges of the query's first item
+        bool skip = dense != 0;
+        if (!SEED && prune && !skip) {
+            if (li == 0 && seeded && first <= kSeedEdges) {
+                skip = true;  // the seed launch did all of it
+            } else if (gk != 0u && __fadd_ru(key2f(ub), P->prune_slack) < keep_threshold(gk, sm.two_err)) {
+                skip = true;
+                atomicAdd(&sm.c_skipped, 1ull);
+            }
+        }
+        if (skip) continue;
+        int64_t e0 = li * chunk, e1 = min(e0 + chunk, s_near);
+        uint32_t k0 = dsc.y, k1 = dsc.z;
+        if (li == 0 && seeded && first > kSeedEdges) {
+            const uint2 sk = P->seed_k[iq];
+            if (SEED) {
+                e1 = kSeedEdges;  // last edge kSeedEdges - 1
+                k1 = sk.x;
+            } else {
+                e0 = kSeedEdges;  // first edge kSeedEdges
+                k0 = sk.y;
+            }
+        }
+        out.item = it;
+        out.q = iq;
+        out.e0 = static_cast<uint32_t>(e0);
+        out.e1 = static_cast<uint32_t>(e1);
+        out.k0 = k0;
+        out.k1 = k1;
+        out.gk = gk;
+        out.ub = ub;
+        return;
+    }
+}
+
 // SEED: with bound pruning on, a first launch processes only the first work
 // item of every query (its highest-bound rows when rows are ordered), so the
 // shared K-th score of every query is set before the main launch starts.
@@ -929,12 +1016,13 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
 #define MHR_SUB(i) ((void)0)
 #endif
     int cur_q = -1;
-    int victim = 0;  // thread 0: offset of the range it currently drains
     if (threadIdx.x == 0) {
         sm.q = -1;
         sm.two_err = 2.0 * P->err_path;
         sm.total_items = P->item_off[nq];
         sm.c_scanned = sm.c_hits = sm.c_cands = sm.c_skipped = 0ull;
+        sm.victim = 0;
+        sm.nx_ready = 0;
     }
     // fast hit scorer: fp32 rows of at most 2G vectors per lane group
     const int vec4 = g.d / 4;
@@ -947,80 +1035,38 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
 
     for (;;) {
         if (threadIdx.x == 0) {
-            // Take the next work item that cannot be skipped, and prepare it: the
-            // item is skipped without touching the CTA's query state when its
-            // query is being recomputed exactly, when the seed launch did all of
-            // it, or when no row of it can reach the query's kept band.
-            const int64_t total_items = sm.total_items;
-            int64_t it = total_items;
-            int iq = -1;
-            unsigned long long probes = 0;
-            for (;;) {
-                MHR_COUNT(c_iter);
-                it = total_items;
-                if (SEED) {
-                    // one item per seeded query: its first one
-                    if (prune) {
-                        for (;;) {
-                            const int qq = static_cast<int>(atomicAdd(&P->counters[kCntSeed], 1ull));
-                            if (qq >= nq) break;
-                            if (seeded_query(P, qq, prune)) {
-                                it = P->item_off[qq];
-                                break;
-                            }
-                        }
-                    }
-                } else {
-                    it = take_item(P, total_items, victim, probes);
-                }
-                if (it >= total_items) break;
-                const uint4 dsc = P->item_desc[it];
-                const uint32_t ub = P->item_ub[it];
-                iq = static_cast<int>(dsc.x & 0x7fffffffu);
-                const bool seeded = (dsc.x >> 31) != 0u;
-                const int64_t li = dsc.w;
-                const int dense = __ldcg(P->dense + iq);
-                uint32_t gk = __ldcg(P->thr_g + iq);
-                const int64_t s_near = P->s_near[iq];
-                if (iq == sm.q && sm.lt_key > gk) gk = sm.lt_key;
-                const int64_t chunk = P->chunk;
-                const int64_t first = min(chunk, s_near);  // edges of the query's first item
-                bool skip = dense != 0;
-                if (!SEED && prune && !skip) {
-                    if (li == 0 && seeded && first <= kSeedEdges) {
-                        skip = true;  // the seed launch did all of it
-                    } else if (gk != 0u && __fadd_ru(key2f(ub), P->prune_slack) < keep_threshold(gk, sm.two_err)) {
-                        skip = true;
+            unsigned long long iters = 0, probes = 0;
+            ItemSel sel;
+            bool have = false;
+            if (!SEED && sm.nx_ready) {
+                // the item taken during the last score phase, unless the band rose past it since
+                sm.nx_ready = 0;
+                sel = sm.nx;
+                have = true;
+                if (prune && sel.item < sm.total_items) {
+                    uint32_t gk = sel.gk;
+                    if (sel.q == sm.q && sm.lt_key > gk) gk = sm.lt_key;
+                    if (gk != 0u && __fadd_ru(key2f(sel.ub), P->prune_slack) < keep_threshold(gk, sm.two_err)) {
                         ++sm.c_skipped;
-                    }
-                }
-                if (skip) continue;
-                // edge range and the near entries holding its first and last edge
-                int64_t e0 = li * chunk, e1 = min(e0 + chunk, s_near);
-                uint32_t k0 = dsc.y, k1 = dsc.z;
-                if (li == 0 && seeded && first > kSeedEdges) {
-                    const uint2 sk = P->seed_k[iq];
-                    if (SEED) {
-                        e1 = kSeedEdges;  // last edge kSeedEdges - 1
-                        k1 = sk.x;
+                        have = false;
                     } else {
-                        e0 = kSeedEdges;  // first edge kSeedEdges
-                        k0 = sk.y;
+                        sel.gk = gk;
                     }
                 }
-                sm.e0 = static_cast<uint32_t>(e0);
-                sm.e1 = static_cast<uint32_t>(e1);
-                sm.k0 = k0;
-                sm.k1 = k1;
-                sm.f_gk = gk;
-                break;
             }
+            if (!have) select_item<SEED>(sm, P, nq, prune, sel, iters, probes);
 #ifdef MHR_PHASE_TIMING
+            c_iter += iters;
             c_probe += probes;
 #endif
-            sm.item = it;
-            sm.skip = iq;  // temporarily: the item's query
-            if (it < total_items) MHR_COUNT(c_items);
+            sm.item = sel.item;
+            sm.skip = sel.q;  // temporarily: the item's query
+            sm.e0 = sel.e0;
+            sm.e1 = sel.e1;
+            sm.k0 = sel.k0;
+            sm.k1 = sel.k1;
+            sm.f_gk = sel.gk;
+            if (sel.item < sm.total_items) MHR_COUNT(c_items);
         }
         __syncthreads();
         const int64_t item = sm.item;
@@ -1429,6 +1475,13 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                 }
             }
             MHR_WEND(wt_score);
+            if (!SEED && done && warp == kMidWarps - 1 && lane == 0 && !sm.nx_ready) {
+                // The last warp gets the fewest hit batches: once they are scored it
+                // takes the next item while the other warps finish theirs.
+                unsigned long long iters = 0, probes = 0;
+                select_item<SEED>(sm, P, nq, prune, sm.nx, iters, probes);
+                sm.nx_ready = 1;
+            }
             if (!__syncthreads_or(done ? 0 : 1)) break;
             flush_cands(sm, P, K);
         }
@@ -1542,29 +1595,37 @@ __global__ void __launch_bounds__(1024) k_merge1(const PlanDev* __restrict__ P) 
 // sequential sum of edge e of candidate c straight from the three embedding
 // rows (16-byte loads, several in flight), so thirty independent chains share
 // the warp.
-constexpr int kRsWarps = 8;
+constexpr int kRsWarps = 4;
 constexpr int kRsCands = 10;
 
-__device__ __forceinline__ double term64(const DevGraph& g, uint32_t h, uint32_t r, uint32_t t, int j) {
-    const double a = emb_f64(g.vemb, g.dtype, h, g.d, j);
-    const double b = emb_f64(g.remb, g.dtype, r, g.d, j);
-    const double c = emb_f64(g.vemb, g.dtype, t, g.d, j);
-    if (g.fn == MHR_SCORE_TRANSE_L1) return fabs(__dsub_rn(__dadd_rn(a, b), c));
-    return __dmul_rn(__dmul_rn(a, b), c);
+// Exact binary32 -> binary64 widening done with integer operations (the value
+// is finite: the graph load rejects NaN and infinity), keeping the slow fp64
+// pipe for the arithmetic: sign and mantissa move over, the exponent is
+// re-biased (1023 - 127 = 896), and a subnormal is first normalised.
+__device__ __forceinline__ double widen(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint64_t sign = static_cast<uint64_t>(u >> 31) << 63;
+    uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    if (e == 0u) {
+        if (m == 0u) return __longlong_as_double(static_cast<long long>(sign));
+        const int sh = __clz(m) - 8;  // moves the top set bit to position 23
+        m = (m << sh) & 0x7fffffu;
+        e = static_cast<uint32_t>(1 - sh);
+    }
+    const uint64_t bits = sign | (static_cast<uint64_t>(e + 896u) << 52) | (static_cast<uint64_t>(m) << 29);
+    return __longlong_as_double(static_cast<long long>(bits));
+}
+
+__device__ __forceinline__ double term1(float a, float b, float c, bool transe) {
+    const double x = widen(a), y = widen(b), z = widen(c);
+    return transe ? fabs(__dsub_rn(__dadd_rn(x, y), z)) : __dmul_rn(__dmul_rn(x, y), z);
 }
 
 __device__ __forceinline__ double acc4(double acc, const float4& a, const float4& b, const float4& c, bool transe) {
-    if (transe) {
-        acc = __dadd_rn(acc, fabs(__dsub_rn(__dadd_rn(static_cast<double>(a.x), static_cast<double>(b.x)), static_cast<double>(c.x))));
-        acc = __dadd_rn(acc, fabs(__dsub_rn(__dadd_rn(static_cast<double>(a.y), static_cast<double>(b.y)), static_cast<double>(c.y))));
-        acc = __dadd_rn(acc, fabs(__dsub_rn(__dadd_rn(static_cast<double>(a.z), static_cast<double>(b.z)), static_cast<double>(c.z))));
-        acc = __dadd_rn(acc, fabs(__dsub_rn(__dadd_rn(static_cast<double>(a.w), static_cast<double>(b.w)), static_cast<double>(c.w))));
-    } else {
-        acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(static_cast<double>(a.x), static_cast<double>(b.x)), static_cast<double>(c.x)));
-        acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(static_cast<double>(a.y), static_cast<double>(b.y)), static_cast<double>(c.y)));
-        acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(static_cast<double>(a.z), static_cast<double>(b.z)), static_cast<double>(c.z)));
-        acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(static_cast<double>(a.w), static_cast<double>(b.w)), static_cast<double>(c.w)));
-    }
+    acc = __dadd_rn(acc, term1(a.x, b.x, c.x, transe));
+    acc = __dadd_rn(acc, term1(a.y, b.y, c.y, transe));
+    acc = __dadd_rn(acc, term1(a.z, b.z, c.z, transe));
+    acc = __dadd_rn(acc, term1(a.w, b.w, c.w, transe));
     return acc;
 }
 
@@ -1581,7 +1642,9 @@ __device__ __forceinline__ double edge_w64_seq(const DevGraph& g, uint32_t h, ui
 #pragma unroll 4
         for (int j = 0; j < n4; ++j) acc = acc4(acc, __ldg(A + j), __ldg(B + j), __ldg(C + j), transe);
     } else {
-        for (int j = 0; j < d; ++j) acc = __dadd_rn(acc, term64(g, h, r, t, j));
+        for (int j = 0; j < d; ++j)
+            acc = __dadd_rn(acc, term1(emb_f32(g.vemb, g.dtype, h, d, j), emb_f32(g.remb, g.dtype, r, d, j),
+                                       emb_f32(g.vemb, g.dtype, t, d, j), transe));
     }
     return transe ? __dsub_rn(g.gamma, acc) : acc;
 }
@@ -1591,11 +1654,13 @@ __global__ void __launch_bounds__(kRsWarps * 32) k_rescore(const PlanDev* __rest
     const int nq = P->nq, cap = P->band_cap;
     const int64_t gw = blockIdx.x * static_cast<int64_t>(kRsWarps) + w;
     const int64_t nw = static_cast<int64_t>(gridDim.x) * kRsWarps;
-    // work unit = (query, group of ten band entries)
+    // work unit u = (group of ten band entries) * nq + query: the units that
+    // have work (the first groups of every query) fill the first warps, spread
+    // over all SMs by the small blocks
     const int64_t groups_per_q = (cap + kRsCands - 1) / kRsCands;
     for (int64_t u = gw; u < static_cast<int64_t>(nq) * groups_per_q; u += nw) {
-        const int q = static_cast<int>(u / groups_per_q);
-        const int i0 = static_cast<int>(u - static_cast<int64_t>(q) * groups_per_q) * kRsCands;
+        const int q = static_cast<int>(u % nq);
+        const int i0 = static_cast<int>(u / nq) * kRsCands;
         const int nb = P->band_cnt[q];
         if (i0 >= nb || P->dense[q]) continue;
         const int nc = min(kRsCands, nb - i0);
@@ -2158,7 +2223,9 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precisio
     if ((rc = plan_alloc(p, &h.out, static_cast<size_t>(nq) * K)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.n_out, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.counters, kCntCount)) != MHR_OK) return bail(rc);
-    if ((rc = plan_alloc(p, &h.partials, kScanGrid + 1)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.partials, kScanPartials)) != MHR_OK) return bail(rc);
+    if (cudaMemset(h.partials, 0, sizeof(int64_t) * kScanPartials) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "cudaMemset (scan counter)"));
     if ((rc = plan_alloc(p, &h.cursors, p->grid)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.drained, (p->grid + 31) / 32)) != MHR_OK) return bail(rc);
     h.grid = p->grid;

@@ -54,36 +54,47 @@ __device__ __forceinline__ T block_sum(T x, T* smem) {
 
 // ---------------------------------------------------------------------------
 // Device-wide exclusive scan over n = *n_dev elements: out[i] = sum in[0..i),
-// out[n] = total.  Three launches with a fixed grid of kScanGrid blocks; each
-// block owns one contiguous range.  `partials` holds kScanGrid + 1 int64.
+// out[n] = total.  Two launches with a fixed grid of kScanGrid blocks; each
+// block owns one contiguous range.  `partials` holds kScanPartials int64: the
+// block sums, the total, and a completion counter that must be zero before
+// the first scan (the last block resets it).
 // ---------------------------------------------------------------------------
+constexpr int kScanPartials = kScanGrid + 2;
+
+// block sums; the last block to finish turns them into exclusive offsets
 template <typename TIn>
 __global__ void __launch_bounds__(kScanThreads)
-scan_partials_kernel(const TIn* __restrict__ in, const int64_t* __restrict__ n_dev,
-                     int64_t* __restrict__ partials) {
+scan_partials_kernel(const TIn* __restrict__ in, const int64_t* __restrict__ n_dev, int64_t* __restrict__ partials) {
     __shared__ int64_t sm[33];
+    __shared__ int last;
     const int64_t n = *n_dev;
     const int64_t per = (n + gridDim.x - 1) / gridDim.x;
     const int64_t lo = blockIdx.x * per, hi = min(n, lo + per);
     int64_t acc = 0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += static_cast<int64_t>(in[i]);
-    int64_t tot = block_sum(acc, sm);
-    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
-}
-
-static __global__ void __launch_bounds__(kScanThreads)
-scan_top_kernel(int64_t* __restrict__ partials, int nparts) {
-    __shared__ int64_t sm[33];
-    int64_t carry = 0;
-    for (int base = 0; base < nparts; base += blockDim.x) {
-        int i = base + threadIdx.x;
-        int64_t v = i < nparts ? partials[i] : 0;
-        int64_t tot;
-        int64_t ex = block_excl_scan(v, sm, &tot);
-        if (i < nparts) partials[i] = ex + carry;
-        carry += tot;
+    const int64_t tot = block_sum(acc, sm);
+    unsigned long long* done = reinterpret_cast<unsigned long long*>(partials + gridDim.x + 1);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = tot;
+        __threadfence();
+        last = atomicAdd(done, 1ull) == gridDim.x - 1;
     }
-    if (threadIdx.x == 0) partials[nparts] = carry;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    int64_t carry = 0;
+    for (int base = 0; base < static_cast<int>(gridDim.x); base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int64_t v = i < static_cast<int>(gridDim.x) ? __ldcg(partials + i) : 0;
+        int64_t t;
+        const int64_t ex = block_excl_scan(v, sm, &t);
+        if (i < static_cast<int>(gridDim.x)) partials[i] = ex + carry;
+        carry += t;
+    }
+    if (threadIdx.x == 0) {
+        partials[gridDim.x] = carry;
+        *done = 0ull;
+    }
 }
 
 template <typename TIn>
@@ -110,7 +121,6 @@ template <typename TIn>
 inline cudaError_t device_excl_scan(const TIn* in, const int64_t* n_dev, int64_t* partials,
                                     int64_t* out, cudaStream_t st) {
     scan_partials_kernel<TIn><<<kScanGrid, kScanThreads, 0, st>>>(in, n_dev, partials);
-    scan_top_kernel<<<1, kScanThreads, 0, st>>>(partials, kScanGrid);
     scan_apply_kernel<TIn><<<kScanGrid, kScanThreads, 0, st>>>(in, n_dev, partials, out);
     return cudaGetLastError();
 }

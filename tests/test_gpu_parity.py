@@ -421,3 +421,29 @@ def test_autotune_picks_a_candidate_and_keeps_results(mhr):
     with pytest.raises(mhr.MhrError):
         mhr.mhr_topk_paths_batched(G, S, T, 30, opts={"tile": 6})
     G.close()
+
+
+@pytest.mark.parametrize("fn", ["transe", "distmult"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_subnormal_and_signed_zero_embeddings(mhr, fn, dtype):
+    """Embedding tables holding subnormals, +0 and -0 next to ordinary values:
+    the fp64 rescoring widens every stored value exactly, so scores stay
+    bit-identical to the oracle's."""
+    rng = np.random.default_rng(77)
+    g = random_kg(rng, 150, 2500, 4, 16)
+    vemb = g.vemb.copy()
+    remb = g.remb.copy()
+    for tab in (vemb, remb):
+        mask = rng.random(tab.shape)
+        tab[mask < 0.15] = np.float32(1e-40) * rng.choice([-1.0, 1.0], size=int((mask < 0.15).sum())).astype(np.float32)
+        tab[(mask >= 0.15) & (mask < 0.2)] = np.float32(-0.0)
+        tab[(mask >= 0.2) & (mask < 0.25)] = np.float32(0.0)
+        tab[(mask >= 0.25) & (mask < 0.3)] = np.float32(2.0 ** -126)
+    assert np.any(np.abs(vemb[vemb != 0]) < np.float32(1.1754944e-38))
+    if dtype == "bf16":
+        g.vemb, g.remb, g.dtype = synth.to_bf16_bits(vemb), synth.to_bf16_bits(remb), "bf16"
+    else:
+        g.vemb, g.remb = vemb, remb
+    S = rng.integers(0, g.n, 12).astype(np.uint32)
+    T = rng.integers(0, g.n, 12).astype(np.uint32)
+    run_and_compare(mhr, g, S, T, 25, fn)
