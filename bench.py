@@ -288,11 +288,15 @@ def run_gpu(args):
         if args.chunk > 0:
             o["chunk"] = args.chunk
         elif args.chunk < 0:
-            # launch shape (work-item size, scan tile) from the library's autotuner,
-            # on this batch, before timing
+            # launch shape (work-item size, scan tile) and, for DistMult, the
+            # middle-edge screen from the library's autotuner, on this batch,
+            # before timing
             if form not in tuned:
-                tuned[form] = mhr.mhr_autotune(G, dS, dT, K, opts=o, stream=stream)
-            o["chunk"], o["tile"] = tuned[form][0], tuned[form][1]
+                to = dict(o)
+                if tc and form != "plain":
+                    to["precision"] = -1
+                tuned[form] = mhr.mhr_autotune(G, dS, dT, K, opts=to, stream=stream)
+            o["chunk"], o["tile"], o["precision"] = tuned[form][0], tuned[form][1], tuned[form][2]
         return o
 
     opts = make_opts(args.form)
@@ -300,6 +304,8 @@ def run_gpu(args):
     def step(o, with_stats=False):
         return mhr.mhr_topk_paths_batched(G, dS, dT, K, out=out, n_out=n_out, stream=stream,
                                           opts=o, with_stats=with_stats)
+
+    dense_steps = []
 
     def timed(o, steps, sampler=None):
         for _ in range(args.warmup):
@@ -320,6 +326,7 @@ def run_gpu(args):
             ev[i][1].record(stream)
             join_ms.append(st["ms_join"])
             dev_ms.append(st["ms_device"])
+            dense_steps.append(st["dense_queries"])
         torch.cuda.synchronize()
         clk = sampler.stop() if sampler else None
         el = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), ws, "cuda")
@@ -342,6 +349,8 @@ def run_gpu(args):
                       "ms_per_step": o_ms / o_steps, "join_ms": statistics.mean(o_join),
                       "chunk": tuned[of][0] if of in tuned else args.chunk,
                       "tile": tuned[of][1] if of in tuned else None,
+                      "middle_edge_screen": (("bf16 tensor cores" if tuned[of][2] else "fp32 CUDA cores")
+                                             if of in tuned else None),
                       "work_per_step": {k: o_stats[k] for k in ("edges_scanned", "hits", "paths", "pruned_edges")}}
         if of == "plain":
             o_stats_plain = o_stats
@@ -384,13 +393,15 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": DATA,
             "config": {"workload": WORKLOAD_DESC, "queries_per_step": nq, "K": K,
                        "score_fn": score_fn, "form": FORM_DESC[args.form],
-                       "middle_edge_screen": "bf16 tensor cores (hi/lo split)" if (tc and args.form != "plain") else "fp32 CUDA cores",
+                       "middle_edge_screen": ("bf16 tensor cores (hi/lo split)" if opts.get("precision") == 1
+                                              else "fp32 CUDA cores"),
                        "l2": "flushed before every step (256 MiB write, excluded from the step time)",
                        "parallelism": "replicas (each rank its own queries)" if ws > 1 else "single GPU",
                        "launch": "three CUDA graphs per step (before / join / after)",
                        "chunk": opts.get("chunk", "library default"),
                        "tile": opts.get("tile", "library default"),
-                       "autotune_ms": ({f"{c}x{t}": v for (c, t), v in tuned[args.form][2].items()}
+                       "autotune_ms": ({f"{'tc' if p else 'fp32'}/{c}x{t}": v
+                                        for (p, c, t), v in tuned[args.form][3].items()}
                                        if args.form in tuned else None)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * nq,
                     "d2h_bytes_per_step": nq * K * 24 + 4 * nq},
@@ -413,6 +424,9 @@ def run_gpu(args):
                                "loss_first": train_rep.loss_first, "loss_last": train_rep.loss_last,
                                "train_s": train_s} if train_rep else None),
             "device_ms_per_step": statistics.mean(dev_ms),
+            "device_ms_spread": {"min": min(dev_ms), "median": statistics.median(dev_ms), "max": max(dev_ms)},
+            "join_ms_spread": {"min": min(join_ms), "median": statistics.median(join_ms), "max": max(join_ms)},
+            "steps_with_dense_queries": sum(1 for x in dense_steps if x),
             "device_host_agree": agree,
             "wall_s_timed_loop": wall1 - wall0,
         }

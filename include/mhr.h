@@ -194,20 +194,26 @@ mhr_status mhr_topk_paths_batched(const mhr_graph* g, int32_t nq, const uint32_t
  * Launch-shape autotuner for the batched search (the paper has no
  * counterpart; its OpenMP loops have no tunable shape).  Runs
  * mhr_topk_paths_batched on the nq queries (s, t; mem applies to both) with
- * opts and every pair (chunks[i], tiles[j]) as (opts->chunk, opts->tile):
- * chunks are multiples of 32 in [32, 16384] (NULL: {4096, 8192, 16384},
- * n_chunks = 3), tiles are 4 or 8 (NULL: {4, 8}, n_tiles = 2).  Each pair gets
- * one untimed run, then reps timed runs, timed by CUDA events around the
- * launch sequence on cuda_stream; ms_out[i * n_tiles + j] (optional, host) =
- * the fastest of the pair's runs; *best_chunk and *best_tile (host) = the pair
- * with the lowest time (the first one on ties).  Every run computes the same
- * result (discarded).  Keeps the winner's buffers and releases the others'.
- * Synchronous.  MHR_EINVAL on bad arguments or candidates.
+ * opts and every combination of
+ *   - middle-edge screen: opts->precision, or, when opts->precision < 0, both
+ *     0 (fp32 CUDA cores) and 1 (bf16 tensor cores; only for DistMult with at
+ *     most 16 relations);
+ *   - work-item size chunks[i]: multiples of 32 in [32, 16384] (NULL:
+ *     {4096, 8192, 16384}, n_chunks = 3);
+ *   - scan tile tiles[j]: 4 or 8 (NULL: {4, 8}, n_tiles = 2).
+ * Each combination gets one untimed run, then reps timed runs, timed by CUDA
+ * events around the launch sequence on cuda_stream; ms_out (optional, host)
+ * receives the fastest time of each combination at
+ * [(p * n_chunks + i) * n_tiles + j], p indexing the screens tried in the
+ * order above; *best_chunk, *best_tile and *best_precision (optional) (host)
+ * = the fastest combination (the first one on ties).  Every run computes the
+ * same result (discarded).  Keeps the winner's buffers and releases the
+ * others'.  Synchronous.  MHR_EINVAL on bad arguments or candidates.
  */
 mhr_status mhr_autotune(const mhr_graph* g, int32_t nq, const uint32_t* s, const uint32_t* t, int32_t K,
                         mhr_mem mem, const mhr_query_opts* opts, const int32_t* chunks, int32_t n_chunks,
                         const int32_t* tiles, int32_t n_tiles, int32_t reps, int32_t* best_chunk,
-                        int32_t* best_tile, float* ms_out, void* cuda_stream);
+                        int32_t* best_tile, int32_t* best_precision, float* ms_out, void* cuda_stream);
 
 /*
  * Learned ordering (the paper has no learned component; this implements the

@@ -113,7 +113,7 @@ def load_library(build_if_missing: bool = True):
                                                ctypes.POINTER(QueryOpts), ctypes.POINTER(Stats), P]
         lib.mhr_autotune.restype = ctypes.c_int
         lib.mhr_autotune.argtypes = [P, i32, P, P, i32, ctypes.c_int, ctypes.POINTER(QueryOpts), P, i32, P, i32,
-                                     i32, ctypes.POINTER(i32), ctypes.POINTER(i32), P, P]
+                                     i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), P, P]
         lib.mhr_training_labels.restype = ctypes.c_int
         lib.mhr_training_labels.argtypes = [P, i32, P, P, i64, P, P, P, P, ctypes.POINTER(i64), P]
         lib.mhr_mlp_features.restype = ctypes.c_int
@@ -335,22 +335,30 @@ def mhr_topk_paths_batched(g: Graph, S, T, K: int, out=None, n_out=None, opts=No
 
 def mhr_autotune(g: Graph, S, T, K: int, opts=None, chunks=(4096, 8192, 16384), tiles=(4, 8),
                  reps: int = 3, stream=None):
-    """Time the batched search on (S, T) for every (work-item size, scan tile)
-    pair; returns (best chunk, best tile, {(chunk, tile): ms})."""
+    """Time the batched search on (S, T) for every (screen, work-item size,
+    scan tile) combination (both screens when opts["precision"] < 0); returns
+    (best chunk, best tile, best precision, {(precision, chunk, tile): ms})."""
     lib = load_library()
     mem = _mem_of(S, T)
     if mem == MHR_MEM_HOST:
         S, T = _host(S, np.uint32), _host(T, np.uint32)
     ch = np.ascontiguousarray(chunks, dtype=np.int32)
     tl = np.ascontiguousarray(tiles, dtype=np.int32)
-    ms = np.zeros(len(ch) * len(tl), dtype=np.float32)
-    bc, bt = ctypes.c_int32(0), ctypes.c_int32(0)
+    ms = np.zeros(2 * len(ch) * len(tl), dtype=np.float32)
+    bc, bt, bp = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
     o = _opts(opts)
     _check(lib.mhr_autotune(g.handle, int(S.shape[0]), _ptr(S), _ptr(T), int(K), mem,
                             ctypes.byref(o) if o is not None else None, _ptr(ch), len(ch), _ptr(tl), len(tl),
-                            int(reps), ctypes.byref(bc), ctypes.byref(bt), _ptr(ms), _stream_ptr(stream)))
-    table = {(int(c), int(t)): float(ms[i * len(tl) + j]) for i, c in enumerate(ch) for j, t in enumerate(tl)}
-    return int(bc.value), int(bt.value), table
+                            int(reps), ctypes.byref(bc), ctypes.byref(bt), ctypes.byref(bp), _ptr(ms),
+                            _stream_ptr(stream)))
+    req = o.precision if o is not None else 0
+    precs = ([0, 1] if (g.score_fn == MHR_SCORE_DISTMULT and g.R <= 16) else [0]) if req < 0 else [req]
+    table = {}
+    for p_i, pr in enumerate(precs):
+        for i, c in enumerate(ch):
+            for j, t in enumerate(tl):
+                table[(pr, int(c), int(t))] = float(ms[(p_i * len(ch) + i) * len(tl) + j])
+    return int(bc.value), int(bt.value), int(bp.value), table
 
 
 def mhr_topk_paths_noalloc(g: Graph, s: int, t: int, K: int, out, n_out, stream=None):

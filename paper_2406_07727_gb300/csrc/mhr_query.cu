@@ -620,14 +620,35 @@ __device__ void flush_cands(MidSmem& sm, const PlanDev* __restrict__ P, int K) {
     }
     __syncthreads();
     compact_cands(sm, sm.thr_keep);
+    // A band still denser than kDenseLimit goes to the query's pool now, which
+    // frees the buffer; only a full pool sends the query to the exact path.
     if (threadIdx.x == 0) {
+        sm.pool_off = -1;
         if (sm.cand_cnt > kDenseLimit && !sm.local_dense) {
-            sm.local_dense = 1;
-            atomicExch(&P->dense[sm.q], 1);
+            const int n = sm.cand_cnt;
+            const int off = atomicAdd(&P->pool_cnt[sm.q], n);
+            if (off + n > P->pq) {
+                sm.local_dense = 1;
+                atomicExch(&P->dense[sm.q], 1);
+#ifdef MHR_PHASE_TIMING
+                printf("MHR_DENSE spill q %d blk %d off %d n %d lt %.6f keep %.6f two_err %.6g\n", sm.q, blockIdx.x,
+                       off, n, key2f(sm.lt_key), sm.thr_keep, sm.two_err);
+#endif
+            } else {
+                sm.pool_off = off;
+                sm.c_cands += static_cast<unsigned long long>(n);
+            }
         }
-        sm.round_cnt = sm.cand_cnt;
+        sm.round_cnt = sm.pool_off >= 0 ? 0 : sm.cand_cnt;
     }
     __syncthreads();
+    if (sm.pool_off >= 0) {
+        Cand* dst = P->pool + static_cast<int64_t>(sm.q) * P->pq + sm.pool_off;
+        for (int i = threadIdx.x; i < sm.cand_cnt; i += blockDim.x) dst[i] = sm.cand[i];
+        __syncthreads();
+        if (threadIdx.x == 0) sm.cand_cnt = 0;
+        __syncthreads();
+    }
 }
 
 // final flush of the current query into its candidate pool
@@ -638,7 +659,12 @@ __device__ void finish_query(MidSmem& sm, const PlanDev* __restrict__ P, int K) 
         if (!sm.local_dense && sm.cand_cnt > 0) {
             const int n = sm.cand_cnt;
             const int off = atomicAdd(&P->pool_cnt[sm.q], n);
-            if (off + n > P->pq) atomicExch(&P->dense[sm.q], 1);
+            if (off + n > P->pq) {
+                atomicExch(&P->dense[sm.q], 1);
+#ifdef MHR_PHASE_TIMING
+                printf("MHR_DENSE pool q %d blk %d off %d n %d lt %.6f\n", sm.q, blockIdx.x, off, n, key2f(sm.lt_key));
+#endif
+            }
             else sm.pool_off = off;
             sm.c_cands += static_cast<unsigned long long>(n);
         }
@@ -716,12 +742,18 @@ __device__ __forceinline__ float term4(const float4& h, const float4& r, const f
 }
 
 // fp32 weight of the middle edge (u, r, v) for the f32 rows with d = 4*vec,
-// vec <= 2G: lane `sub` of a group of G owns vectors sub and sub + G.  The
+// vec <= kHitVecs*G: lane `sub` of a group of G owns vectors sub + k*G.  The
 // near-side row (the scanned vertex) stays in registers across the group's
 // consecutive hits, the relation row comes from shared memory when cached,
-// and only the far-side row is fetched per hit.
+// and only the far-side row is fetched per hit (its kHitVecs loads issued
+// together).
+#ifndef MHR_HIT_VECS
+#define MHR_HIT_VECS 2
+#endif
+constexpr int kHitVecs = MHR_HIT_VECS;  // 16-byte vectors per lane and row in the hit scorer
+
 struct NearRow {
-    float4 a, b;
+    float4 v[kHitVecs];
     uint32_t id;
 };
 
@@ -730,27 +762,28 @@ __device__ __forceinline__ float hit_w32_f32(const DevGraph& g, NearRow& nr, uin
                                              const float4* relc) {
     const float* E = static_cast<const float*>(g.vemb);
     const float* Rw = static_cast<const float*>(g.remb);
-    const bool has0 = sub < vec, has1 = sub + G < vec;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool has[kHitVecs];
+#pragma unroll
+    for (int k = 0; k < kHitVecs; ++k) has[k] = sub + k * G < vec;
     if (near_v != nr.id) {
-        nr.a = has0 ? ld4(E, near_v, g.d, sub) : make_float4(0.f, 0.f, 0.f, 0.f);
-        nr.b = has1 ? ld4(E, near_v, g.d, sub + G) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < kHitVecs; ++k) nr.v[k] = has[k] ? ld4(E, near_v, g.d, sub + k * G) : z;
         nr.id = near_v;
     }
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 f0 = has0 ? ld4(E, far_v, g.d, sub) : z;
-    const float4 f1 = has1 ? ld4(E, far_v, g.d, sub + G) : z;
-    float4 r0, r1;
-    if (relc) {
-        r0 = has0 ? relc[r * vec + sub] : z;
-        r1 = has1 ? relc[r * vec + sub + G] : z;
-    } else {
-        r0 = has0 ? ld4(Rw, r, g.d, sub) : z;
-        r1 = has1 ? ld4(Rw, r, g.d, sub + G) : z;
+    float4 f[kHitVecs], rv[kHitVecs];
+#pragma unroll
+    for (int k = 0; k < kHitVecs; ++k) f[k] = has[k] ? ld4(E, far_v, g.d, sub + k * G) : z;
+#pragma unroll
+    for (int k = 0; k < kHitVecs; ++k) {
+        if (relc) rv[k] = has[k] ? relc[r * vec + sub + k * G] : z;
+        else rv[k] = has[k] ? ld4(Rw, r, g.d, sub + k * G) : z;
     }
     const bool transe = g.fn == MHR_SCORE_TRANSE_L1;
-    float acc;
-    if (fwd) acc = (has0 ? term4(nr.a, r0, f0, transe) : 0.f) + (has1 ? term4(nr.b, r1, f1, transe) : 0.f);
-    else acc = (has0 ? term4(f0, r0, nr.a, transe) : 0.f) + (has1 ? term4(f1, r1, nr.b, transe) : 0.f);
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < kHitVecs; ++k)
+        acc += has[k] ? (fwd ? term4(nr.v[k], rv[k], f[k], transe) : term4(f[k], rv[k], nr.v[k], transe)) : 0.f;
     for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
     return transe ? __fsub_rn(g.gamma32, acc) : acc;
 }
@@ -1026,7 +1059,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
     }
     // fast hit scorer: fp32 rows of at most 2G vectors per lane group
     const int vec4 = g.d / 4;
-    const bool fast = g.dtype == MHR_F32 && (g.d & 3) == 0 && vec4 <= 2 * P->score_width;
+    const bool fast = g.dtype == MHR_F32 && (g.d & 3) == 0 && vec4 <= kHitVecs * P->hit_width;
     const bool relc_ok = fast && g.R * vec4 <= kRelCacheVecs;
     if (relc_ok)
         for (int i = threadIdx.x; i < g.R * vec4; i += blockDim.x)
@@ -1290,7 +1323,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         const ListEnt* nearL = P->nearL + sm.near_base;  // ordered position
         const float* w1s = P->w32 + sm.a_base;
         const float* w3s = P->w32 + sm.c_base;
-        const int G = P->score_width, H = 32 / G;
+        const int G = P->hit_width, H = 32 / G;
         const int sub = lane & (G - 1);
         int b = warp;              // current batch of 32 hits
         bool loaded = false;
@@ -1579,6 +1612,9 @@ __global__ void __launch_bounds__(1024) k_merge1(const PlanDev* __restrict__ P) 
             if (w > P->band_cap) {
                 atomicExch(&P->dense[q], 1);
                 P->band_cnt[q] = 0;
+#ifdef MHR_PHASE_TIMING
+                printf("MHR_DENSE band q %d w %d pc %d thr %.6f\n", q, w, pc, thr);
+#endif
             } else {
                 P->band_cnt[q] = w;
                 atomicAdd(&P->counters[kCntRescored], static_cast<unsigned long long>(w));
@@ -2152,10 +2188,10 @@ static cudaError_t launch_graphs(Plan* p, cudaStream_t st) {
     return cudaEventRecord(p->ev[3], st);
 }
 
-// lanes that score one edge together: about two 16-byte vectors per lane per row
-static int hit_group_width(int d, int dtype) {
+// lanes that score one edge together: about `per` 16-byte vectors per lane per row
+static int hit_group_width(int d, int dtype, int per) {
     const int vec = (dtype == MHR_F32) ? ((d & 3) == 0 ? d / 4 : d) : ((d & 7) == 0 ? d / 8 : d);
-    const int want = (vec + 1) / 2;
+    const int want = (vec + per - 1) / per;
     int w = 1;
     while (w < want && w < 32) w <<= 1;
     return w;
@@ -2187,13 +2223,14 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precisio
     h.chunk = chunk;
     h.sigma = choose_sigma(G->dg.n);
     h.nbw = static_cast<int32_t>(((G->dg.n - 1) >> h.sigma) / 32 + 1);
-    h.pq = 8 * K + 2048;
+    h.pq = 16 * K + 4096;  // room for the final candidates of every CTA that worked on the query
     h.band_cap = K + 2048;
     h.err_path = precision ? G->err_path_tc : G->err_path;
     h.precision = precision;
     h.prune_slack = precision ? __double2float_ru_host((G->epstc_edge + G->eps32_edge) * 1.01) : 0.f;
     h.wsplit = G->wsplit;
-    h.score_width = hit_group_width(G->dg.d, G->dg.dtype);
+    h.score_width = hit_group_width(G->dg.d, G->dg.dtype, 2);
+    h.hit_width = hit_group_width(G->dg.d, G->dg.dtype, kHitVecs);
     mhr_status rc = MHR_OK;
     auto bail = [&](mhr_status r) {
         delete p;
@@ -2437,13 +2474,14 @@ extern "C" mhr_status mhr_topk_paths_batched(const mhr_graph* gc, int32_t nq, co
     return MHR_OK;
 }
 
-// Autotuner of the join's launch shape: every (work-item size, scan tile)
-// candidate runs the same batch (results do not depend on either), timed by
-// the plan's own events; the plans of the losing candidates are released.
+// Autotuner of the join's launch shape and middle-edge screen: every
+// (screen, work-item size, scan tile) candidate runs the same batch (results
+// do not depend on any of them), timed by the plan's own events; the plans of
+// the losing candidates are released.
 extern "C" mhr_status mhr_autotune(const mhr_graph* gc, int32_t nq, const uint32_t* s, const uint32_t* t, int32_t K,
                                    mhr_mem mem, const mhr_query_opts* opts, const int32_t* chunks, int32_t n_chunks,
                                    const int32_t* tiles, int32_t n_tiles, int32_t reps, int32_t* best_chunk,
-                                   int32_t* best_tile, float* ms_out, void* cuda_stream) {
+                                   int32_t* best_tile, int32_t* best_precision, float* ms_out, void* cuda_stream) {
     MHR_TRY(check_graph(gc));
     mhr_graph* G = const_cast<mhr_graph*>(gc);
     static const int32_t kChunks[3] = {4096, 8192, 16384};
@@ -2466,16 +2504,29 @@ extern "C" mhr_status mhr_autotune(const mhr_graph* gc, int32_t nq, const uint32
             return fail(MHR_EINVAL, "chunk candidates must be multiples of 32 in [32, 16384]");
     for (int i = 0; i < n_tiles; ++i)
         if (tiles[i] != 4 && tiles[i] != 8) return fail(MHR_EINVAL, "tile candidates must be 4 or 8");
+    mhr_query_opts o = opts ? *opts : mhr_query_opts{};
+    // screens to try: the requested one, or both when opts->precision < 0 and
+    // the tensor-core screen applies (DistMult, at most 16 relations)
+    int precs[2] = {o.precision, 0};
+    int n_prec = 1;
+    if (o.precision < 0) {
+        precs[0] = 0;
+        if (G->fn == MHR_SCORE_DISTMULT && G->dg.R <= 16 && G->wsplit) {
+            precs[1] = 1;
+            n_prec = 2;
+        }
+    }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     std::vector<uint32_t> hs(nq), ht(nq);
     MHR_CUDA_TRY(cudaMemcpyAsync(hs.data(), s, sizeof(uint32_t) * nq, cudaMemcpyDefault, st));
     MHR_CUDA_TRY(cudaMemcpyAsync(ht.data(), t, sizeof(uint32_t) * nq, cudaMemcpyDefault, st));
     MHR_CUDA_TRY(cudaStreamSynchronize(st));
-    mhr_query_opts o = opts ? *opts : mhr_query_opts{};
+    const int per = n_chunks * n_tiles;
     int best = -1;
     float best_ms = 0.f;
-    for (int i = 0; i < n_chunks * n_tiles; ++i) {
-        o.chunk = chunks[i / n_tiles];
+    for (int i = 0; i < n_prec * per; ++i) {
+        o.precision = precs[i / per];
+        o.chunk = chunks[(i % per) / n_tiles];
         o.tile = tiles[i % n_tiles];
         Plan* p = nullptr;
         MHR_TRY(run_batch(G, nq, hs.data(), ht.data(), K, &o, st, &p));  // warm-up (capture, buffers)
@@ -2493,15 +2544,16 @@ extern "C" mhr_status mhr_autotune(const mhr_graph* gc, int32_t nq, const uint32
             best_ms = ms;
         }
     }
-    *best_chunk = chunks[best / n_tiles];
+    const int bp = precs[best / per];
+    *best_chunk = chunks[(best % per) / n_tiles];
     *best_tile = tiles[best % n_tiles];
+    if (best_precision) *best_precision = bp;
     // keep only the winner's plan
     MHR_CUDA_TRY(cudaStreamSynchronize(st));
-    for (int i = 0; i < n_chunks * n_tiles; ++i) {
-        const int c = chunks[i / n_tiles], tl = tiles[i % n_tiles];
-        if (c == *best_chunk && tl == *best_tile) continue;
-        auto it = G->plans->plans.find(std::make_tuple(static_cast<int>(nq), static_cast<int>(K), c,
-                                                       static_cast<int>(o.precision), tl));
+    for (int i = 0; i < n_prec * per; ++i) {
+        const int pr = precs[i / per], c = chunks[(i % per) / n_tiles], tl = tiles[i % n_tiles];
+        if (pr == bp && c == *best_chunk && tl == *best_tile) continue;
+        auto it = G->plans->plans.find(std::make_tuple(static_cast<int>(nq), static_cast<int>(K), c, pr, tl));
         if (it != G->plans->plans.end()) {
             delete it->second;
             G->plans->plans.erase(it);

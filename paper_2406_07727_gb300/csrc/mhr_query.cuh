@@ -72,7 +72,8 @@ enum {
 // a captured CUDA graph keeps working when buffers are regrown between calls.
 struct PlanDev {
     int32_t nq, K, chunk, sigma;
-    int32_t nbw, pq, band_cap, score_width;
+    int32_t nbw, pq, band_cap, score_width;  // score_width: lanes per edge in the expansion
+    int32_t hit_width;                        // lanes per middle edge in the join's hit scorer
     int32_t grid, prune;  // persistent CTAs of the join; bound pruning on/off
     int32_t order, label;  // near-row order: 0 natural, 1 by bound, 2 by learned score; label dump on/off
     int32_t precision;     // 0 fp32 CUDA-core middle-edge screen, 1 bf16 tensor-core screen (DistMult)

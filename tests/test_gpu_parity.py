@@ -403,9 +403,9 @@ def test_autotune_picks_a_candidate_and_keeps_results(mhr):
     G = mhr.load_kg(g)
     opts = {"prune": 1, "order": 1}
     chunks, tiles = (64, 512, 2048), (4, 8)
-    bc, bt, ms = mhr.mhr_autotune(G, S, T, 30, opts=opts, chunks=chunks, tiles=tiles, reps=2)
-    assert bc in chunks and bt in tiles and set(ms) == {(c, t) for c in chunks for t in tiles}
-    assert all(v > 0 for v in ms.values()) and ms[(bc, bt)] == min(ms.values())
+    bc, bt, bp, ms = mhr.mhr_autotune(G, S, T, 30, opts=opts, chunks=chunks, tiles=tiles, reps=2)
+    assert bc in chunks and bt in tiles and bp == 0 and set(ms) == {(0, c, t) for c in chunks for t in tiles}
+    assert all(v > 0 for v in ms.values()) and ms[(0, bc, bt)] == min(ms.values())
     out_b, n_b = mhr.mhr_topk_paths_batched(G, S, T, 30, opts={**opts, "chunk": bc, "tile": bt})
     out_d, n_d = mhr.mhr_topk_paths_batched(G, S, T, 30)
     assert np.array_equal(n_b, n_d)
@@ -420,6 +420,25 @@ def test_autotune_picks_a_candidate_and_keeps_results(mhr):
         mhr.mhr_autotune(G, S, T, 30, tiles=(5,))
     with pytest.raises(mhr.MhrError):
         mhr.mhr_topk_paths_batched(G, S, T, 30, opts={"tile": 6})
+    G.close()
+
+
+def test_autotune_chooses_the_screen_for_distmult(mhr):
+    """With precision -1 the autotuner also times the bf16 tensor-core screen
+    against the fp32 one (DistMult, <= 16 relations) and returns the faster;
+    both give the oracle's lists."""
+    g = synth.gen_rmat_kg(13, 6000, 80_000, 8, 3, seed=43)
+    g.vemb, g.remb = synth.gen_embeddings(g.n, g.R, 32, 1 / 8, seed=43)
+    S, T = synth.queries_edge_biased(g, 16, seed=43)
+    G = mhr.load_kg(g, score_fn="distmult")
+    bc, bt, bp, ms = mhr.mhr_autotune(G, S, T, 20, opts={"prune": 1, "order": 1, "precision": -1},
+                                      chunks=(1024,), tiles=(4,), reps=1)
+    assert set(ms) == {(0, 1024, 4), (1, 1024, 4)} and bp in (0, 1) and ms[(bp, bc, bt)] == min(ms.values())
+    want, n_want = oracle.topk_paths_batch(g, S, T, 20, fn="distmult")
+    for prec in (0, 1):
+        out, n = mhr.mhr_topk_paths_batched(G, S, T, 20, opts={"prune": 1, "order": 1, "precision": prec})
+        for q in range(len(S)):
+            compare_query(out[q], n[q], want[q][: n_want[q]], ctx=(prec, q))
     G.close()
 
 
