@@ -197,6 +197,9 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, D
     const int nq = P->nq;
     const int64_t warp_id = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    // rows of at most two 16-byte vectors per lane: unrolled scorer
+    const bool vec2 = g.dtype == MHR_F32 ? ((g.d & 3) == 0 && (g.d >> 2) <= 2 * G)
+                                         : ((g.d & 7) == 0 && (g.d >> 3) <= 2 * G);
     for (int64_t base = warp_id * 32; base < X; base += nwarps * 32) {  // warp-uniform
         const int64_t x = base + lane;
         const bool live = x < X;
@@ -232,7 +235,8 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, D
             const uint32_t a = __shfl_sync(0xffffffffu, hu, src);
             const uint32_t rr = __shfl_sync(0xffffffffu, r, src);
             const uint32_t b = __shfl_sync(0xffffffffu, tv, src);
-            const float w = edge_w32_group(g, a, rr, b, sub, G);  // dead lanes score vertex 0's rows
+            // dead lanes score vertex 0's rows
+            const float w = vec2 ? edge_w32_group2(g, a, rr, b, sub, G) : edge_w32_group(g, a, rr, b, sub, G);
             const float tw = __shfl_sync(0xffffffffu, w, ((lane - rd * H) & (H - 1)) * G);
             if (lane / H == rd) wmine = tw;
         }
@@ -395,14 +399,20 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_keys(const PlanDev* __restr
         }
         __syncthreads();
         auto a_pair = [&](int r, int k) -> uint32_t { return slot[r] >= 0 ? feature_pair(g, va[r], vb[r], k) : 0u; };
-        auto store_y = [&](int r, float y) {
+        auto store_y = [&](int r, float y) {  // called by the 32 lanes of warp 0, row r = lane
+            uint32_t qid = 0xffffffffu, key = 0u;
             if (slot[r] >= 0) {
                 // order key: the row bound plus the predicted (non-positive) slack
-                const uint32_t key = f2key(__fadd_rn(own[r], fminf(y, 0.f)));
+                key = f2key(__fadd_rn(own[r], fminf(y, 0.f)));
                 P->mlp_pred[slot[r]] = key2f(key);
                 P->okey[slot[r]] = key;
-                atomicMin(&P->qkey[2 * qrow[r]], key);
-                atomicMax(&P->qkey[2 * qrow[r] + 1], key);
+                qid = static_cast<uint32_t>(qrow[r]);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, qid);
+            const uint32_t kmin = __reduce_min_sync(peers, key), kmax = __reduce_max_sync(peers, key);
+            if (qid != 0xffffffffu && r == __ffs(peers) - 1) {
+                atomicMin(&P->qkey[2 * qid], kmin);
+                atomicMax(&P->qkey[2 * qid + 1], kmax);
             }
         };
         auto store_z = [&](int, int, float) {};
@@ -411,30 +421,44 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_keys(const PlanDev* __restr
 }
 
 // row bound of every near entry, its order key and the per-query key range
+// (one atomic per run of lanes with the same query)
 __global__ void k_order_key(const PlanDev* __restrict__ P, DevGraph g) {
     const int64_t X = P->X;
     const int order = P->order;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < X; x += stride) {
-        P->degv3[x] = 0u;
-        P->ubest[x] = 0u;
-        int q;
-        int64_t base;
-        bool sideA;
-        if (!near_slot(P, x, q, base, sideA)) continue;
-        const ListEnt e = P->list[x];
-        // any path through this near entry scores (in fp32) at most:
-        //   forward  (near = u): maxw1(u) + maxw_out(u) + max_v maxw3(v)
-        //   backward (near = v): max_u maxw1(u) + maxw_in(v) + maxw3(v)
-        float b;
-        if (sideA) b = __fadd_rn(__fadd_rn(e.maxw, g.maxw_out[e.vertex]), key2f(P->qmax[2 * q + 1]));
-        else b = __fadd_rn(__fadd_rn(key2f(P->qmax[2 * q]), g.maxw_in[e.vertex]), e.maxw);
-        P->bnat[x] = b;
-        if (order != 1) continue;  // order 2 keys: k_mlp_keys
-        const uint32_t key = f2key(b);
-        P->okey[x] = key;
-        atomicMin(&P->qkey[2 * q], key);
-        atomicMax(&P->qkey[2 * q + 1], key);
+    const int64_t iters = (X + stride - 1) / stride;  // uniform per warp
+    const int64_t first = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t x = first + it * stride;
+        uint32_t qid = 0xffffffffu, key = 0u;
+        if (x < X) {
+            P->degv3[x] = 0u;
+            P->ubest[x] = 0u;
+            int q;
+            int64_t base;
+            bool sideA;
+            if (near_slot(P, x, q, base, sideA)) {
+                const ListEnt e = P->list[x];
+                // any path through this near entry scores (in fp32) at most:
+                //   forward  (near = u): maxw1(u) + maxw_out(u) + max_v maxw3(v)
+                //   backward (near = v): max_u maxw1(u) + maxw_in(v) + maxw3(v)
+                float b;
+                if (sideA) b = __fadd_rn(__fadd_rn(e.maxw, e.midw), key2f(P->qmax[2 * q + 1]));
+                else b = __fadd_rn(__fadd_rn(key2f(P->qmax[2 * q]), e.midw), e.maxw);
+                P->bnat[x] = b;
+                if (order == 1) {  // order 2 keys: k_mlp_keys
+                    key = f2key(b);
+                    P->okey[x] = key;
+                    qid = static_cast<uint32_t>(q);
+                }
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, qid);
+        const uint32_t kmin = __reduce_min_sync(peers, key), kmax = __reduce_max_sync(peers, key);
+        if (qid != 0xffffffffu && (threadIdx.x & 31) == __ffs(peers) - 1) {
+            atomicMin(&P->qkey[2 * qid], kmin);
+            atomicMax(&P->qkey[2 * qid + 1], kmax);
+        }
     }
 }
 
@@ -563,6 +587,8 @@ struct MidSmem {
     int64_t item;
     uint32_t e0, e1, k0, k1;
     int cand_cnt, hit_cnt;
+    int batch_next;  // next batch of 32 hits to score
+    int nx_claim;    // set by the warp that takes the next item
     int round_cnt;  // cand_cnt snapshot taken before the barrier that opens a round
     int pool_off;
     uint32_t lt_key;
@@ -1121,6 +1147,8 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                 sm.thr_keep = keep_threshold(gk, sm.two_err);
             }
             sm.hit_cnt = 0;
+            sm.batch_next = 0;
+            sm.nx_claim = 0;
         }
         __syncthreads();
         if (sm.skip) continue;
@@ -1325,7 +1353,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         const float* w3s = P->w32 + sm.c_base;
         const int G = P->hit_width, H = 32 / G;
         const int sub = lane & (G - 1);
-        int b = warp;              // current batch of 32 hits
+        int b = 0;                 // current batch of 32 hits (taken from a shared counter)
         bool loaded = false;
         unsigned pend = 0;         // lanes whose hit still has combinations to expand
         uint32_t slice = 0;        // this lane's next combination
@@ -1342,8 +1370,19 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                 const float thr = sm.thr_keep;
                 for (;;) {
                     if (!loaded) {
+                        if (lane == 0) b = atomicAdd(&sm.batch_next, 1);
+                        b = __shfl_sync(FULL, b, 0);
                         const int hb = b * 32;
-                        if (hb >= nh) break;
+                        if (hb >= nh) {
+                            // The first warp to find no batch left takes the next work
+                            // item while the other warps finish their last batches.
+                            if (!SEED && lane == 0 && atomicCAS(&sm.nx_claim, 0, 1) == 0) {
+                                unsigned long long iters = 0, probes = 0;
+                                select_item<SEED>(sm, P, nq, prune, sm.nx, iters, probes);
+                                sm.nx_ready = 1;
+                            }
+                            break;
+                        }
                         MHR_SUB_START();
                         const int hi = hb + lane;
                         const bool live = hi < nh;
@@ -1504,17 +1543,9 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                         break;
                     }
                     loaded = false;
-                    b += kMidWarps;
                 }
             }
             MHR_WEND(wt_score);
-            if (!SEED && done && warp == kMidWarps - 1 && lane == 0 && !sm.nx_ready) {
-                // The last warp gets the fewest hit batches: once they are scored it
-                // takes the next item while the other warps finish theirs.
-                unsigned long long iters = 0, probes = 0;
-                select_item<SEED>(sm, P, nq, prune, sm.nx, iters, probes);
-                sm.nx_ready = 1;
-            }
             if (!__syncthreads_or(done ? 0 : 1)) break;
             flush_cands(sm, P, K);
         }
