@@ -58,13 +58,16 @@ __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint3
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// One 32-row tile.  a_pair(r, k) returns the bf16 pair of row r (0..31 within
-// the tile), columns k, k+1.  Writes y for the tile's rows through
-// store_y(r, y) and, if z1 is not null, the pre-activations to z1[r*256 + c]
-// through store_z(r, c, z).  part: shared [32][4] floats.  All 256 threads call.
-template <typename APair, typename StoreY, typename StoreZ>
-__device__ __forceinline__ void mlp_tile(const MlpDev& m, APair a_pair, StoreY store_y, StoreZ store_z, bool want_z,
-                                         float (*part)[4]) {
+// One 32-row tile over the first KT*16 input columns.  a_pair(r, k) returns
+// the bf16 pair of row r (0..31 within the tile), columns k, k+1; bias(r, c)
+// the first-layer bias of hidden unit c for row r (b1[c], or b1[c] plus the
+// product of the columns beyond KT*16 when the caller folded them in).
+// Writes y for the tile's rows through store_y(r, y) and, if want_z, the
+// pre-activations through store_z(r, c, z).  part: shared [32][4] floats.
+// All 256 threads call.
+template <int KT, typename APair, typename Bias, typename StoreY, typename StoreZ>
+__device__ __forceinline__ void mlp_tile_k(const MlpDev& m, APair a_pair, Bias bias, StoreY store_y, StoreZ store_z,
+                                           bool want_z, float (*part)[4]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gq = lane >> 2, tq = lane & 3;
     const int r0 = (warp & 1) * 16;
@@ -74,7 +77,7 @@ __device__ __forceinline__ void mlp_tile(const MlpDev& m, APair a_pair, StoreY s
     for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
     const uint32_t* W = reinterpret_cast<const uint32_t*>(m.W1);
 #pragma unroll 2
-    for (int kt = 0; kt < kMlpIn / 16; ++kt) {
+    for (int kt = 0; kt < KT; ++kt) {
         const int k = kt * 16 + tq * 2;
         const uint32_t a0 = a_pair(r0 + gq, k), a1 = a_pair(r0 + gq + 8, k);
         const uint32_t a2 = a_pair(r0 + gq, k + 8), a3 = a_pair(r0 + gq + 8, k + 8);
@@ -93,8 +96,8 @@ __device__ __forceinline__ void mlp_tile(const MlpDev& m, APair a_pair, StoreY s
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int c = c0 + nt * 8 + tq * 2 + h;
-            const float bb = __ldg(m.b1 + c), ww = __ldg(m.w2 + c);
-            const float z0 = acc[nt][h] + bb, z1 = acc[nt][2 + h] + bb;
+            const float ww = __ldg(m.w2 + c);
+            const float z0 = acc[nt][h] + bias(r0 + gq, c), z1 = acc[nt][2 + h] + bias(r0 + gq + 8, c);
             if (want_z) {
                 store_z(r0 + gq, c, z0);
                 store_z(r0 + gq + 8, c, z1);
@@ -117,6 +120,12 @@ __device__ __forceinline__ void mlp_tile(const MlpDev& m, APair a_pair, StoreY s
         store_y(threadIdx.x, ((pr[0] + pr[1]) + (pr[2] + pr[3])) + __ldg(m.b2));
     }
     __syncthreads();
+}
+
+template <typename APair, typename StoreY, typename StoreZ>
+__device__ __forceinline__ void mlp_tile(const MlpDev& m, APair a_pair, StoreY store_y, StoreZ store_z, bool want_z,
+                                         float (*part)[4]) {
+    mlp_tile_k<kMlpIn / 16>(m, a_pair, [&](int, int c) { return __ldg(m.b1 + c); }, store_y, store_z, want_z, part);
 }
 
 }  // namespace mhr

@@ -366,6 +366,26 @@ __device__ __forceinline__ bool near_slot(const PlanDev* __restrict__ P, int64_t
     return x - base < P->near_cnt[q];
 }
 
+// Learned order, per query: the endpoint half of the first layer, c_q = b1 +
+// W1[:, 128:256] e_end[0:128] (bf16 inputs, fp32 sum), shared by all of the
+// query's near entries.  One block per query, one thread per hidden unit.
+__global__ void __launch_bounds__(kMlpHid) k_mlp_qbias(const PlanDev* __restrict__ P, DevGraph g) {
+    if (P->order != 2) return;
+    const int n = threadIdx.x;
+    const uint32_t* W = reinterpret_cast<const uint32_t*>(P->mlp.W1);
+    for (int q = blockIdx.x; q < P->nq; q += gridDim.x) {
+        const uint32_t vb = P->dir[q] == 1 ? P->T[q] : P->S[q];
+        float acc = __ldg(P->mlp.b1 + n);
+        for (int k = 128; k < kMlpIn; k += 2) {
+            const uint32_t a = feature_pair(g, 0u, vb, k);  // columns k, k+1 of [e_x; e_end]
+            const uint32_t w = __ldg(W + (n * kMlpIn + k) / 2);
+            acc += __uint_as_float(a << 16) * __uint_as_float(w << 16) +
+                   __uint_as_float(a & 0xffff0000u) * __uint_as_float(w & 0xffff0000u);
+        }
+        P->mlp_qbias[static_cast<int64_t>(q) * kMlpHid + n] = acc;
+    }
+}
+
 // Learned order key of every near entry (order 2): the MLP predicts the best
 // completion of a path through the entry from [e_entry; e_far endpoint]; the
 // key adds the entry's own best hop weight.  Tiles of 32 slots.
@@ -398,7 +418,11 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_keys(const PlanDev* __restr
             }
         }
         __syncthreads();
+        // the endpoint half of the input is folded into the per-query bias
         auto a_pair = [&](int r, int k) -> uint32_t { return slot[r] >= 0 ? feature_pair(g, va[r], vb[r], k) : 0u; };
+        auto bias = [&](int r, int c) -> float {
+            return slot[r] >= 0 ? P->mlp_qbias[static_cast<int64_t>(qrow[r]) * kMlpHid + c] : 0.f;
+        };
         auto store_y = [&](int r, float y) {  // called by the 32 lanes of warp 0, row r = lane
             uint32_t qid = 0xffffffffu, key = 0u;
             if (slot[r] >= 0) {
@@ -416,7 +440,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_keys(const PlanDev* __restr
             }
         };
         auto store_z = [&](int, int, float) {};
-        mlp_tile(P->mlp, a_pair, store_y, store_z, false, part);
+        mlp_tile_k<kMlpIn / 32>(P->mlp, a_pair, bias, store_y, store_z, false, part);
     }
 }
 
@@ -1297,9 +1321,13 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                     const uint32_t word = sm.bm[bv >> 5];
                     if ((word >> (bv & 31u)) & 1u) {
                         if (sigma == 0) {
-                            const uint32_t wi = x >> 5;
+                            // set bits before x: the 256-bit block's rank, whole 64-bit
+                            // words of the block below x, the low half of x's 64-bit
+                            // word when x lies in its high half, then x's own word
+                            const uint64_t* bm64 = reinterpret_cast<const uint64_t*>(sm.bm);
                             uint32_t r = sm.rank[x >> 8];
-                            for (uint32_t w = (x >> 8) << 3; w < wi; ++w) r += __popc(sm.bm[w]);
+                            for (uint32_t w = (x >> 8) << 2; w < (x >> 6); ++w) r += __popcll(bm64[w]);
+                            if (x & 32u) r += __popc(sm.bm[(x >> 5) - 1u]);
                             fk = r + __popc(word & ((1u << (x & 31u)) - 1u));
                             hit = true;
                         } else {
@@ -2151,6 +2179,7 @@ static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int
         if (e != cudaSuccess) return e;
         k_plan<<<1, 1024, 0, st>>>(d);
         k_order_key<<<sms * 4, 256, 0, st>>>(d, g);
+        k_mlp_qbias<<<std::min(p->nq, sms * 4), kMlpHid, 0, st>>>(d, g);
         k_mlp_keys<<<sms * 8, kMlpThreads, 0, st>>>(d, g);
         k_order_hist<<<sms * 4, 256, 0, st>>>(d);
         const int64_t* nH = reinterpret_cast<const int64_t*>(p->dregion + offsetof(PlanDev, nhist));
@@ -2276,6 +2305,7 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precisio
     if ((rc = plan_alloc(p, &h.near_off, nq + 1)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.thr_g, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.seed_k, nq)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.mlp_qbias, static_cast<size_t>(nq) * kMlpHid)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.qmax, 2 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.qkey, 2 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.hist, 256 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);

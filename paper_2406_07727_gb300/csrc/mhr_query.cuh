@@ -116,6 +116,7 @@ struct PlanDev {
     uint4* item_desc;   // [item_cap] (query | seeded << 31, near entry holding the item's first
                         //  edge, near entry holding its last edge, index of the item in its query)
     uint2* seed_k;      // [nq] near entries holding edge kSeedEdges - 1 and edge kSeedEdges
+    float* mlp_qbias;   // [nq x 256] learned order: b1 + W1[:, 128:] e_end[0:128] per query
     // per query [nq] (+1 for item_off)
     int32_t* status;
     int32_t* dir;       // 1 = forward (scan out-rows of hop-1 vertices), 0 = backward
