@@ -56,7 +56,10 @@ WORKLOAD_DESCS = {
              "one hub query, K=10, TransE-L1"),
     "precision": ("the medium R-MAT graph (1,000,000 vertices, 20,000,000 edges, 16 relations) with d=256 "
                   "fp32 embeddings ~N(0,1/sqrt(d)); 256 edge-biased queries per step, K=100, DistMult"),
+    "learned": ("the precision workload's graph and 256 queries (d=256 fp32, DistMult) with K=50 "
+                "(or the K given), ordering MLP trained on 20,000 held-out queries"),
 }
+K_OVERRIDE = 0
 WORKLOAD_DESC = WORKLOAD_DESCS[WORKLOAD]
 DATA = "synthetic: seeded R-MAT typed knowledge graph standing in for WikiKG90Mv2"
 FORM_DESC = {"plain": "plain: batched, every middle edge scored, fp32 screen + fp64 rescoring",
@@ -108,6 +111,8 @@ def load_workload(rank: int):
     os.environ.setdefault("MHR_SYNTH_CACHE", os.path.join(tempfile.gettempdir(), "mhr_synth_cache"))
     g, S, T, K, spec = synth.workload(WORKLOAD)
     S, T = rank_queries(g, S, T, rank, WORKLOAD)
+    if K_OVERRIDE:
+        K = K_OVERRIDE
     return g, S, T, K, spec
 
 
@@ -452,11 +457,13 @@ def main():
                     help="medium is the benchmark workload; the others are extra measurements")
     ap.add_argument("--all-forms", type=int, default=1, help="also time the other forms (plain, bound, chosen)")
     ap.add_argument("--train-queries", type=int, default=20000)
+    ap.add_argument("--K", type=int, default=0, help="override the workload's K (e.g. 500 for the learned workload)")
     ap.add_argument("--form", default="chosen", choices=["plain", "bound", "chosen"],
                     help="plain: every hit scored; chosen: provable bound pruning (same output)")
     args = ap.parse_args()
-    global WORKLOAD, WORKLOAD_DESC
+    global WORKLOAD, WORKLOAD_DESC, K_OVERRIDE
     WORKLOAD, WORKLOAD_DESC = args.workload, WORKLOAD_DESCS[args.workload]
+    K_OVERRIDE = args.K
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -175,6 +175,7 @@ __global__ void k_init(const PlanDev* __restrict__ P, DevGraph g) {
         P->dense[q] = 0;
         P->pool_cnt[q] = 0;
         P->band_cnt[q] = 0;
+        P->chain_cnt[q] = 0;
         P->n_out[q] = 0;
     }
     if (tid < kCntCount) P->counters[tid] = 0ull;
@@ -248,6 +249,7 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, D
             P->w32[x] = excl ? neg_inf() : wmine;
             P->flag[x] = head ? 1u : 0u;
             P->degv[x] = 0u;
+            P->w64own[x] = 0;
         }
     }
 }
@@ -1667,10 +1669,39 @@ __global__ void __launch_bounds__(1024) k_merge1(const PlanDev* __restrict__ P) 
             if (keep && w + pos < P->band_cap) band[w + pos] = c;
             w += tot;
         }
+        // fp64 sums the band needs: every middle edge, and each hop-1 / hop-3 edge once
+        if (w <= P->band_cap) {
+            __syncthreads();
+            const int64_t a0 = P->a_off[q], c0 = P->totA + P->c_off[q];
+            uint32_t* ch = P->chains + static_cast<int64_t>(q) * 3 * P->band_cap;
+            int nch = 0;
+            for (int base = 0; base < w; base += blockDim.x) {
+                const int i = base + threadIdx.x;
+                int n = 0;
+                bool o1 = false, o3 = false;
+                Cand c;
+                if (i < w) {
+                    c = band[i];
+                    o1 = atomicExch(&P->w64own[a0 + c.a_idx], 1) == 0;
+                    o3 = atomicExch(&P->w64own[c0 + c.c_idx], 1) == 0;
+                    n = 1 + (o1 ? 1 : 0) + (o3 ? 1 : 0);
+                }
+                int tot;
+                int pos = nch + block_excl_scan(n, red, &tot);
+                if (i < w) {
+                    ch[pos++] = (2u << 30) | static_cast<uint32_t>(i);
+                    if (o1) ch[pos++] = (0u << 30) | c.a_idx;
+                    if (o3) ch[pos++] = (1u << 30) | c.c_idx;
+                }
+                nch += tot;
+            }
+            if (threadIdx.x == 0) P->chain_cnt[q] = nch;
+        }
         if (threadIdx.x == 0) {
             if (w > P->band_cap) {
                 atomicExch(&P->dense[q], 1);
                 P->band_cnt[q] = 0;
+                P->chain_cnt[q] = 0;
 #ifdef MHR_PHASE_TIMING
                 printf("MHR_DENSE band q %d w %d pc %d thr %.6f\n", q, w, pc, thr);
 #endif
@@ -1686,12 +1717,15 @@ __global__ void __launch_bounds__(1024) k_merge1(const PlanDev* __restrict__ P) 
 // fp64 rescoring of the band.  The canonical order fixes the accumulation
 // acc = acc + y_j (j ascending) of each edge; the terms y_j = |(a_j + b_j) - c_j|
 // (or (a_j * b_j) * c_j) are formed from the stored values converted exactly.
-// A warp takes up to ten candidates: lane 3c + e (e = 0, 1, 2) runs the
-// sequential sum of edge e of candidate c straight from the three embedding
-// rows (16-byte loads, several in flight), so thirty independent chains share
-// the warp.
+// k_merge1 lists the sums a query's band needs (every middle edge; each hop-1
+// and hop-3 edge once, however many band entries share it); each lane runs one
+// sum straight from the three embedding rows (16-byte loads, several in
+// flight), and k_merge2 adds the three weights of every entry.
 constexpr int kRsWarps = 4;
-constexpr int kRsCands = 10;
+#ifndef MHR_RS_LANES
+#define MHR_RS_LANES 32
+#endif
+constexpr int kRsLanes = MHR_RS_LANES;  // sums per warp (the other lanes idle)
 
 // Exact binary32 -> binary64 widening done with integer operations (the value
 // is finite: the graph load rejects NaN and infinity), keeping the slow fp64
@@ -1749,46 +1783,47 @@ __global__ void __launch_bounds__(kRsWarps * 32) k_rescore(const PlanDev* __rest
     const int nq = P->nq, cap = P->band_cap;
     const int64_t gw = blockIdx.x * static_cast<int64_t>(kRsWarps) + w;
     const int64_t nw = static_cast<int64_t>(gridDim.x) * kRsWarps;
-    // work unit u = (group of ten band entries) * nq + query: the units that
-    // have work (the first groups of every query) fill the first warps, spread
-    // over all SMs by the small blocks
-    const int64_t groups_per_q = (cap + kRsCands - 1) / kRsCands;
+    // work unit u = (group of kRsLanes sums) * nq + query: the units that have work
+    // (the first groups of every query) fill the first warps, spread over all
+    // SMs by the small blocks; lane = one sequential fp64 sum
+    const int64_t groups_per_q = (3 * static_cast<int64_t>(cap) + kRsLanes - 1) / kRsLanes;
     for (int64_t u = gw; u < static_cast<int64_t>(nq) * groups_per_q; u += nw) {
         const int q = static_cast<int>(u % nq);
-        const int i0 = static_cast<int>(u / nq) * kRsCands;
-        const int nb = P->band_cnt[q];
-        if (i0 >= nb || P->dense[q]) continue;
-        const int nc = min(kRsCands, nb - i0);
-        const int64_t x0 = static_cast<int64_t>(q) * cap + i0;
+        const int i0 = static_cast<int>(u / nq) * kRsLanes;
+        const int nc = P->chain_cnt[q];
+        if (i0 >= nc || P->dense[q]) continue;
+        const int i = i0 + lane;
+        if (lane >= kRsLanes || i >= nc) continue;
+        const uint32_t chv = P->chains[static_cast<int64_t>(q) * 3 * cap + i];
+        const uint32_t kind = chv >> 30, idx = chv & 0x3fffffffu;
         const uint32_t s = P->S[q], t = P->T[q];
-        const int c = lane / 3, e = lane - 3 * (lane / 3);  // candidate, edge
-        double we = 0.0;
-        mhr_path p;
-        if (c < nc) {
-            const Cand cd = P->band_cand[x0 + c];
-            const int64_t p1 = g.off[s] + cd.a_idx;
-            const int64_t p3 = g.roff[t] + cd.c_idx;
-            p.u = g.col[p1];
-            p.r1 = g.rel[p1];
-            p.v = g.rcol[p3];
-            p.r3 = g.rrel[p3];
-            p.r2 = cd.r2;
-            p.pad = 0;
-            const uint32_t h = e == 0 ? s : (e == 1 ? p.u : p.v);
-            const uint32_t r = e == 0 ? p.r1 : (e == 1 ? p.r2 : p.r3);
-            const uint32_t tt = e == 0 ? p.u : (e == 1 ? p.v : t);
-            we = edge_w64_seq(g, h, r, tt);
+        // the edge and where its weight goes; then one converged call for all lanes
+        uint32_t h, r, tt;
+        double* dst;
+        if (kind == 0u) {  // hop-1 edge (s, r1, u)
+            const int64_t p1 = g.off[s] + idx;
+            h = s;
+            r = g.rel[p1];
+            tt = g.col[p1];
+            dst = P->w64s + P->a_off[q] + idx;
+        } else if (kind == 1u) {  // hop-3 edge (v, r3, t)
+            const int64_t p3 = g.roff[t] + idx;
+            h = g.rcol[p3];
+            r = g.rrel[p3];
+            tt = t;
+            dst = P->w64s + P->totA + P->c_off[q] + idx;
+        } else {  // middle edge (u, r2, v) of band entry idx
+            const Cand cd = P->band_cand[static_cast<int64_t>(q) * cap + idx];
+            h = g.col[g.off[s] + cd.a_idx];
+            r = cd.r2;
+            tt = g.rcol[g.roff[t] + cd.c_idx];
+            dst = P->band_w2 + static_cast<int64_t>(q) * cap + idx;
         }
-        const int b = 3 * (c < nc ? c : 0);
-        const double w1 = __shfl_sync(FULL, we, b), w2 = __shfl_sync(FULL, we, b + 1), w3 = __shfl_sync(FULL, we, b + 2);
-        if (c < nc && e == 0) {
-            p.score = __dadd_rn(__dadd_rn(w1, w2), w3);
-            P->band_path[x0 + c] = p;
-        }
+        *dst = edge_w64_seq(g, h, r, tt);
     }
 }
 
-__global__ void __launch_bounds__(1024) k_merge2(const PlanDev* __restrict__ P) {
+__global__ void __launch_bounds__(1024) k_merge2(const PlanDev* __restrict__ P, DevGraph g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     mhr_path* buf = reinterpret_cast<mhr_path*>(smem_raw);
     const int K = P->K;
@@ -1801,8 +1836,26 @@ __global__ void __launch_bounds__(1024) k_merge2(const PlanDev* __restrict__ P) 
         const int nb = P->band_cnt[q];
         int m = 2;
         while (m < nb) m <<= 1;
-        const mhr_path* src = P->band_path + static_cast<int64_t>(q) * P->band_cap;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) buf[i] = i < nb ? src[i] : worst_path();
+        // band entries with their fp64 score (w1 + w2) + w3 in the canonical order
+        const Cand* bc = P->band_cand + static_cast<int64_t>(q) * P->band_cap;
+        const double* bw2 = P->band_w2 + static_cast<int64_t>(q) * P->band_cap;
+        const uint32_t s = P->S[q], t = P->T[q];
+        const int64_t a0 = P->a_off[q], c0 = P->totA + P->c_off[q];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            mhr_path p = worst_path();
+            if (i < nb) {
+                const Cand cd = bc[i];
+                const int64_t p1 = g.off[s] + cd.a_idx, p3 = g.roff[t] + cd.c_idx;
+                p.u = g.col[p1];
+                p.r1 = g.rel[p1];
+                p.v = g.rcol[p3];
+                p.r3 = g.rrel[p3];
+                p.r2 = cd.r2;
+                p.pad = 0;
+                p.score = __dadd_rn(__dadd_rn(P->w64s[a0 + cd.a_idx], bw2[i]), P->w64s[c0 + cd.c_idx]);
+            }
+            buf[i] = p;
+        }
         __syncthreads();
         block_sort_paths(buf, m);
         const int nout = min(nb, K);
@@ -2090,7 +2143,7 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
     if (X <= p->slot_cap && p->slot_mem) return MHR_OK;
     int64_t cap = std::max<int64_t>(X, std::max<int64_t>(p->slot_cap * 2, 1 << 16));
     // per slot: w32 4, flag 4, degv 4, scan1 8, scan2 8, list 32, nearP 8, nearL 32, nearB 4,
-    // okey 4, orank 4, bnat 4, nperm 4, degv3 4, scan4 8, mlp_pred 4, ubest 4
+    // okey 4, orank 4, bnat 4, nperm 4, degv3 4, scan4 8, mlp_pred 4, ubest 4, w64s 8, w64own 4
     const size_t a8 = 256;
     size_t o = 0;
     const size_t o_w32 = o; o = align_up(o + 4 * cap, a8);
@@ -2110,6 +2163,8 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
     const size_t o_s4 = o; o = align_up(o + 8 * (cap + 1), a8);
     const size_t o_mlp = o; o = align_up(o + 4 * cap, a8);
     const size_t o_ub = o; o = align_up(o + 4 * cap, a8);
+    const size_t o_w64 = o; o = align_up(o + 8 * cap, a8);
+    const size_t o_own = o; o = align_up(o + 4 * cap, a8);
     void* mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, o);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (frontier slots)");
@@ -2137,6 +2192,8 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
     p->h.scan4 = reinterpret_cast<int64_t*>(b + o_s4);
     p->h.mlp_pred = reinterpret_cast<float*>(b + o_mlp);
     p->h.ubest = reinterpret_cast<uint32_t*>(b + o_ub);
+    p->h.w64s = reinterpret_cast<double*>(b + o_w64);
+    p->h.w64own = reinterpret_cast<int32_t*>(b + o_own);
     // scan kernels take raw pointers, so a new buffer needs a new capture
     p->drop_graphs();
     return MHR_OK;
@@ -2211,7 +2268,7 @@ static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int
     } else {
         k_merge1<<<std::min(p->nq, sms * 2), 1024, 0, st>>>(d);
         k_rescore<<<sms * 4, kRsWarps * 32, 0, st>>>(d, g);
-        k_merge2<<<std::min(p->nq, sms * 2), 1024, merge2_smem_bytes(p->h.band_cap), st>>>(d);
+        k_merge2<<<std::min(p->nq, sms * 2), 1024, merge2_smem_bytes(p->h.band_cap), st>>>(d, g);
         k_exact<<<std::min(p->nq, sms * 2), 1024, exact_smem_bytes(), st>>>(d, g);
     }
     return cudaGetLastError();
@@ -2317,7 +2374,9 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precisio
     if ((rc = plan_alloc(p, &h.hits, static_cast<size_t>(p->grid) * kMaxChunk)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.pool, static_cast<size_t>(nq) * h.pq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.band_cand, static_cast<size_t>(nq) * h.band_cap)) != MHR_OK) return bail(rc);
-    if ((rc = plan_alloc(p, &h.band_path, static_cast<size_t>(nq) * h.band_cap)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.band_w2, static_cast<size_t>(nq) * h.band_cap)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.chains, static_cast<size_t>(nq) * 3 * h.band_cap)) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.chain_cnt, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.out, static_cast<size_t>(nq) * K)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.n_out, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.counters, kCntCount)) != MHR_OK) return bail(rc);

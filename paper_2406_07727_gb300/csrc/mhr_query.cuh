@@ -109,6 +109,8 @@ struct PlanDev {
     int64_t* scan4;     // prefix of degv3
     float* mlp_pred;    // learned order key (order 2)
     uint32_t* ubest;    // label dump: key of the best fp32 path through a near entry (ordered position)
+    double* w64s;       // fp64 weight of a hop-1 / hop-3 slot used by the band
+    int32_t* w64own;    // 1 once a band entry has claimed the slot's fp64 sum
     uint32_t* qkey;     // [2 nq] min / max order key per query
     uint32_t* hist;     // [nq * 256] bucket counts
     int64_t* hscan;     // [nq * 256 + 1]
@@ -134,7 +136,9 @@ struct PlanDev {
     Hit* hits;          // [grid x kMaxChunk]
     Cand* pool;         // [nq x pq]
     Cand* band_cand;    // [nq x band_cap]
-    mhr_path* band_path;// [nq x band_cap]
+    double* band_w2;    // [nq x band_cap] fp64 weight of each band entry's middle edge
+    uint32_t* chains;   // [nq x 3 band_cap] fp64 sums to run: kind << 30 | index
+    int32_t* chain_cnt; // [nq]
     mhr_path* out;      // [nq x K]
     int32_t* n_out;     // [nq]
     unsigned long long* counters;  // kCntCount

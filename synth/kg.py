@@ -313,6 +313,9 @@ WORKLOADS = {
     # the medium graph with d=256; 256 queries, K = 100, DistMult
     "precision": dict(kind="rmat", scale=20, n=1_000_000, E=20_000_000, R=16, n_types=6, d=256,
                       var=None, dtype="f32", queries="edge", nq=256, K=100, score="distmult"),
+    # learned ordering: the precision graph and queries with K = 50 (K = 500 by override)
+    "learned": dict(kind="rmat", scale=20, n=1_000_000, E=20_000_000, R=16, n_types=6, d=256,
+                    var=None, dtype="f32", queries="edge", nq=256, K=50, score="distmult"),
     # R-MAT scale 24 cut to 10M vertices, 200M edges, 32 relations, d=128 bf16;
     # 4096 queries with log-uniform source degree in [1, 1e5], K = 50
     "batching": dict(kind="rmat", scale=24, n=10_000_000, E=200_000_000, R=32, n_types=6, d=128,

@@ -140,7 +140,8 @@ def test_training_labels_match_path_enumeration(mhr):
     G.close()
 
 
-def test_learned_order_keeps_results_and_reports_work(mhr):
+@pytest.mark.parametrize("K", [50, 500])
+def test_learned_order_keeps_results_and_reports_work(mhr, K):
     """Train on held-out queries, then compare natural, bound and learned
     orders (with bound pruning) against the plain search: identical results;
     the work each order prunes is recorded."""
@@ -151,17 +152,17 @@ def test_learned_order_keeps_results_and_reports_work(mhr):
     G = mhr.load_kg(g)
     model, rep = mhr.train_ordering_mlp(G, St, Tt, epochs=4, batch=2048, lr=2e-3)
     assert rep.rows > 1000 and rep.loss_last < rep.loss_first
-    base, nb = mhr.mhr_topk_paths_batched(G, S, T, 50)
+    base, nb = mhr.mhr_topk_paths_batched(G, S, T, K)
     work = {}
     for name, opts in (("natural", {"prune": 1, "order": 0}), ("bound", {"prune": 1, "order": 1}),
                        ("learned", {"prune": 1, "order": 2, "mlp": model})):
-        out, n, st = mhr.mhr_topk_paths_batched(G, S, T, 50, opts=opts, with_stats=True)
+        out, n, st = mhr.mhr_topk_paths_batched(G, S, T, K, opts=opts, with_stats=True)
         assert np.array_equal(n, nb)
         for q in range(len(S)):
             assert out[q][: n[q]].tobytes() == base[q][: nb[q]].tobytes()
         work[name] = (st["edges_scanned"], st["hits"], st["pruned_edges"])
     print("work (scanned, hits, pruned):", work, "train rows", rep.rows)
-    want, n_want = oracle.topk_paths_batch(g, S[:4], T[:4], 50)
+    want, n_want = oracle.topk_paths_batch(g, S[:4], T[:4], K)
     for q in range(4):
         assert base[q][: nb[q]]["u"].tolist() == want[q][: n_want[q]]["u"].tolist()
     G.close()
