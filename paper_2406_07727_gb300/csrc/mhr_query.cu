@@ -611,6 +611,7 @@ struct MidSmem {
     int64_t near_base, far_base, a_base, c_base, s_near;
     // per-item state
     int64_t item;
+    int item_q;  // the item's query
     uint32_t e0, e1, k0, k1;
     int cand_cnt, hit_cnt;
     int batch_next;  // next batch of 32 hits to score
@@ -1145,7 +1146,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
             c_probe += probes;
 #endif
             sm.item = sel.item;
-            sm.skip = sel.q;  // temporarily: the item's query
+            sm.item_q = sel.q;
             sm.e0 = sel.e0;
             sm.e1 = sel.e1;
             sm.k0 = sel.k0;
@@ -1156,8 +1157,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         __syncthreads();
         const int64_t item = sm.item;
         if (item >= sm.total_items) break;
-        const int q = sm.skip;
-        __syncthreads();
+        const int q = sm.item_q;
         if (q != cur_q) {
             if (cur_q >= 0) finish_query(sm, P, K);
             setup_query(sm, P, q);
@@ -1186,18 +1186,69 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         const float* nearB = P->nearB + sm.near_base;
         const uint32_t s_near32 = static_cast<uint32_t>(sm.s_near);
         const float thr_scan = sm.thr_keep;
-        // --- group -> owning near entry (+1), by marking group starts then a prefix max
-        for (int i = threadIdx.x; i < ngroups; i += blockDim.x) sm.gmap[i] = 0u;
-        __syncthreads();
-        for (uint32_t k = sm.k0 + threadIdx.x; k <= sm.k1; k += blockDim.x) {
-            const uint32_t pk = nearP[k].x;
-            const uint32_t pk1 = (k + 1 < static_cast<uint32_t>(near_cnt)) ? nearP[k + 1].x : s_near32;
-            const uint32_t lo = max(pk, e0), hi = min(pk1, e1);
-            const uint32_t gf = (lo - e0 + 31) / 32;
-            if (e0 + 32 * gf < hi) sm.gmap[gf] = k + 1;
-        }
-        __syncthreads();
-        {
+        // --- group -> owning near entry (+1) and, for a group inside one near row,
+        // the CSR position of its first edge (or a marker: several rows, pruned)
+        const uint32_t k0 = sm.k0, k1 = sm.k1;
+        if (k1 - k0 < 63u) {
+            // At most 63 near rows: every warp holds their prefixes in registers
+            // (entry k0 + j at lane j % 32, register j / 32) and each thread finds
+            // the row of its group by a search over them.
+            const uint32_t nent = k1 - k0 + 1u;
+            uint32_t pA = 0xffffffffu, pB = 0xffffffffu, rA = 0u, rB = 0u;
+            float bA = 0.f, bB = 0.f;
+            if (static_cast<uint32_t>(lane) < nent) {
+                const uint2 t = nearP[k0 + lane];
+                pA = t.x;
+                rA = t.y;
+                if (prune) bA = nearB[k0 + lane];
+            }
+            if (static_cast<uint32_t>(lane) + 32u < nent) {
+                const uint2 t = nearP[k0 + 32u + lane];
+                pB = t.x;
+                rB = t.y;
+                if (prune) bB = nearB[k0 + 32u + lane];
+            }
+            const int gidx = threadIdx.x;  // one group per thread (ngroups <= blockDim.x)
+            const uint32_t gs = e0 + 32u * static_cast<uint32_t>(gidx);
+            // pos = number of rows whose prefix is <= gs (>= 1: row k0 holds e0)
+            int pos = 0;
+#pragma unroll
+            for (int step = 32; step > 0; step >>= 1) {
+                const int j = pos + step - 1;
+                const uint32_t va = __shfl_sync(FULL, pA, j & 31), vb = __shfl_sync(FULL, pB, j & 31);
+                if ((j < 32 ? va : vb) <= gs) pos += step;
+            }
+            const int jr = pos - 1, jn = pos;
+            const uint32_t ra = __shfl_sync(FULL, rA, jr & 31), rb2 = __shfl_sync(FULL, rB, jr & 31);
+            const uint32_t pa = __shfl_sync(FULL, pA, jr & 31), pb = __shfl_sync(FULL, pB, jr & 31);
+            const float ba = __shfl_sync(FULL, bA, jr & 31), bb = __shfl_sync(FULL, bB, jr & 31);
+            const uint32_t na = __shfl_sync(FULL, pA, jn & 31), nb = __shfl_sync(FULL, pB, jn & 31);
+            if (gidx < ngroups) {
+                const uint32_t rowstart = jr < 32 ? ra : rb2, pre = jr < 32 ? pa : pb;
+                const float rowb = jr < 32 ? ba : bb;
+                // the row after it starts at the next prefix; the item's last row reaches e1
+                const uint32_t nxt = static_cast<uint32_t>(jn) < nent ? (jn < 32 ? na : nb) : 0xffffffffu;
+                const uint32_t ge = min(gs + 32u, e1);
+                uint32_t gp = kGposMulti;
+                if (ge <= nxt) {
+                    gp = rowstart + (gs - pre);
+                    if (prune && __fadd_ru(rowb, slack) < thr_scan) gp = kGposPruned;
+                }
+                sm.gmap[gidx] = k0 + static_cast<uint32_t>(jr) + 1u;
+                sm.gpos[gidx] = gp;
+            }
+        } else {
+            // by marking group starts, then a prefix max
+            for (int i = threadIdx.x; i < ngroups; i += blockDim.x) sm.gmap[i] = 0u;
+            __syncthreads();
+            for (uint32_t k = k0 + threadIdx.x; k <= k1; k += blockDim.x) {
+                const uint32_t pk = nearP[k].x;
+                const uint32_t pk1 = (k + 1 < static_cast<uint32_t>(near_cnt)) ? nearP[k + 1].x : s_near32;
+                const uint32_t lo = max(pk, e0), hi = min(pk1, e1);
+                const uint32_t gf = (lo - e0 + 31) / 32;
+                if (e0 + 32 * gf < hi) sm.gmap[gf] = k + 1;
+            }
+            __syncthreads();
             // inclusive prefix max over <= 1024 entries (one per thread)
             uint32_t v = threadIdx.x < ngroups ? sm.gmap[threadIdx.x] : 0u;
 #pragma unroll
@@ -1220,8 +1271,6 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
             if (warp > 0) v = max(v, sm.redu[warp - 1]);
             if (threadIdx.x < ngroups) {
                 sm.gmap[threadIdx.x] = v;
-                // a group inside one near row: CSR position of its first edge, or
-                // the whole group pruned by the row bound
                 const uint32_t kk = v - 1u;
                 const uint32_t gs = e0 + 32u * threadIdx.x;
                 const uint32_t ge = min(gs + 32u, e1);
