@@ -67,10 +67,10 @@ FORM_DESC = {"plain": "plain: batched, every middle edge scored, fp32 screen + f
                       "bound pruning of work items, rows and hits (identical output)",
              "chosen": "chosen: as bound, with rows ordered by the learned MLP score (trained on plain runs "
                        "over 20,000 held-out queries before timing) (identical output)"}
-# kernels per step: k_init, k_expand, scan x2, k_lists, scan x2, k_plan, k_order_key,
+# kernels per step: k_init, k_expand, scan x2, k_lists, k_plan, k_order_key, k_mlp_qbias,
 # k_mlp_keys, k_order_hist, scan x2, k_order_perm, scan x2, k_near, k_middle (seed),
 # k_middle, k_merge1, k_rescore, k_merge2, k_exact
-KERNELS_PER_STEP = 23
+KERNELS_PER_STEP = 22
 
 
 def dist_env():

@@ -172,6 +172,8 @@ __global__ void k_init(const PlanDev* __restrict__ P, DevGraph g) {
         P->thr_g[q] = 0u;
         P->qmax[2 * q] = 0u;
         P->qmax[2 * q + 1] = 0u;
+        P->sdeg_q[2 * q] = 0ull;
+        P->sdeg_q[2 * q + 1] = 0ull;
         P->dense[q] = 0;
         P->pool_cnt[q] = 0;
         P->band_cnt[q] = 0;
@@ -207,11 +209,12 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, D
         uint32_t s = 0, t = 0, vtx = 0, r = 0, prev = 0xffffffffu, sdeg = 0;
         int64_t k = 0;
         bool sideA = true;
+        int q = 0;
         if (live) {
             sideA = x < totA;
             const int64_t lx = sideA ? x : x - totA;
             const int64_t* offs = sideA ? P->a_off : P->c_off;
-            const int q = static_cast<int>(upper_bound_i64(offs, nq + 1, lx) - 1);
+            q = static_cast<int>(upper_bound_i64(offs, nq + 1, lx) - 1);
             k = lx - offs[q];
             s = P->S[q];
             t = P->T[q];
@@ -241,6 +244,8 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, D
             const float tw = __shfl_sync(0xffffffffu, w, ((lane - rd * H) & (H - 1)) * G);
             if (lane / H == rd) wmine = tw;
         }
+        uint32_t key = 0xffffffffu;
+        unsigned long long dsum = 0ull;
         if (live) {
             const bool excl = (vtx == s) || (vtx == t);
             // A vertex with no scan edges can neither be scanned nor be hit, so it
@@ -248,9 +253,16 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, D
             const bool head = !excl && sdeg > 0 && (k == 0 || prev != vtx);
             P->w32[x] = excl ? neg_inf() : wmine;
             P->flag[x] = head ? 1u : 0u;
-            P->degv[x] = 0u;
             P->w64own[x] = 0;
+            key = 2u * static_cast<uint32_t>(q) + (sideA ? 0u : 1u);
+            dsum = head ? sdeg : 0u;
         }
+        // S_f / S_b: scan degrees of the distinct frontier vertices, summed per
+        // (query, side) with one atomic per run of lanes sharing the key
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        unsigned long long tot = 0ull;
+        for (unsigned m = peers; m; m &= m - 1) tot += __shfl_sync(peers, dsum, __ffs(m) - 1);
+        if (key != 0xffffffffu && lane == __ffs(peers) - 1 && tot) atomicAdd(&P->sdeg_q[key], tot);
     }
 }
 
@@ -299,7 +311,6 @@ __global__ void k_lists(const PlanDev* __restrict__ P, DevGraph g) {
             }
             e.pad = 0u;
             P->list[base + j] = e;
-            P->degv[base + j] = e.deg;
             qkey = 2u * static_cast<uint32_t>(q) + (sideA ? 0u : 1u);
             mkey = f2key(mw);
         }
@@ -326,8 +337,8 @@ __global__ void __launch_bounds__(1024) k_plan(const PlanDev* __restrict__ P) {
             const int64_t c0 = totA + P->c_off[q], c1 = totA + P->c_off[q + 1];
             const int64_t du = P->scan1[a1] - P->scan1[a0];
             const int64_t dv = P->scan1[c1] - P->scan1[c0];
-            const int64_t sf = P->scan2[a1] - P->scan2[a0];
-            const int64_t sb = P->scan2[c1] - P->scan2[c0];
+            const int64_t sf = static_cast<int64_t>(P->sdeg_q[2 * q]);
+            const int64_t sb = static_cast<int64_t>(P->sdeg_q[2 * q + 1]);
             const bool fwd = sf <= sb;
             const int64_t near_cnt = fwd ? du : dv, far_cnt = fwd ? dv : du;
             const int64_t s_near = (P->status[q] == 0 && far_cnt > 0) ? (fwd ? sf : sb) : 0;
@@ -2191,15 +2202,13 @@ static size_t merge2_smem_bytes(int band_cap) {
 static mhr_status ensure_slots(Plan* p, int64_t X) {
     if (X <= p->slot_cap && p->slot_mem) return MHR_OK;
     int64_t cap = std::max<int64_t>(X, std::max<int64_t>(p->slot_cap * 2, 1 << 16));
-    // per slot: w32 4, flag 4, degv 4, scan1 8, scan2 8, list 32, nearP 8, nearL 32, nearB 4,
+    // per slot: w32 4, flag 4, scan1 8, list 32, nearP 8, nearL 32, nearB 4,
     // okey 4, orank 4, bnat 4, nperm 4, degv3 4, scan4 8, mlp_pred 4, ubest 4, w64s 8, w64own 4
     const size_t a8 = 256;
     size_t o = 0;
     const size_t o_w32 = o; o = align_up(o + 4 * cap, a8);
     const size_t o_flag = o; o = align_up(o + 4 * cap, a8);
-    const size_t o_degv = o; o = align_up(o + 4 * cap, a8);
     const size_t o_s1 = o; o = align_up(o + 8 * (cap + 1), a8);
-    const size_t o_s2 = o; o = align_up(o + 8 * (cap + 1), a8);
     const size_t o_list = o; o = align_up(o + sizeof(ListEnt) * cap, a8);
     const size_t o_near = o; o = align_up(o + sizeof(uint2) * cap, a8);
     const size_t o_nearl = o; o = align_up(o + sizeof(ListEnt) * cap, a8);
@@ -2226,9 +2235,7 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
     unsigned char* b = static_cast<unsigned char*>(mem);
     p->h.w32 = reinterpret_cast<float*>(b + o_w32);
     p->h.flag = reinterpret_cast<uint32_t*>(b + o_flag);
-    p->h.degv = reinterpret_cast<uint32_t*>(b + o_degv);
     p->h.scan1 = reinterpret_cast<int64_t*>(b + o_s1);
-    p->h.scan2 = reinterpret_cast<int64_t*>(b + o_s2);
     p->h.list = reinterpret_cast<ListEnt*>(b + o_list);
     p->h.nearP = reinterpret_cast<uint2*>(b + o_near);
     p->h.nearL = reinterpret_cast<ListEnt*>(b + o_nearl);
@@ -2281,8 +2288,6 @@ static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int
         cudaError_t e = device_excl_scan<uint32_t>(p->h.flag, nX, p->h.partials, p->h.scan1, st);
         if (e != cudaSuccess) return e;
         k_lists<<<sms * 4, 256, 0, st>>>(d, g);
-        e = device_excl_scan<uint32_t>(p->h.degv, nX, p->h.partials, p->h.scan2, st);
-        if (e != cudaSuccess) return e;
         k_plan<<<1, 1024, 0, st>>>(d);
         k_order_key<<<sms * 4, 256, 0, st>>>(d, g);
         k_mlp_qbias<<<std::min(p->nq, sms * 4), kMlpHid, 0, st>>>(d, g);
@@ -2413,6 +2418,7 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precisio
     if ((rc = plan_alloc(p, &h.seed_k, nq)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.mlp_qbias, static_cast<size_t>(nq) * kMlpHid)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.qmax, 2 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);
+    if ((rc = plan_alloc(p, &h.sdeg_q, 2 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.qkey, 2 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.hist, 256 * static_cast<size_t>(nq))) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.hscan, 256 * static_cast<size_t>(nq) + 1)) != MHR_OK) return bail(rc);

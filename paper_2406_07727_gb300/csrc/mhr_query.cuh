@@ -95,8 +95,6 @@ struct PlanDev {
     uint32_t* flag;
     int64_t* scan1;
     ListEnt* list;
-    uint32_t* degv;
-    int64_t* scan2;
     uint2* nearP;  // (prefix of scan degree within the query, row start)
     ListEnt* nearL;  // near entries in ordered position
     float* nearB;  // upper bound of the fp32 score of any path through a near entry
@@ -129,6 +127,7 @@ struct PlanDev {
     int64_t* near_off;  // [nq+1] prefix of near_cnt (rows of the learned-order MLP)
     uint32_t* thr_g;    // order-preserving key of the best known K-th fp32 score
     uint32_t* qmax;     // [2 nq] keys: max hop-1 weight, max hop-3 weight
+    unsigned long long* sdeg_q;  // [2 nq] S_f and S_b: scan degrees of the distinct frontier vertices
     int32_t* dense;
     int32_t* pool_cnt;
     int32_t* band_cnt;
