@@ -221,7 +221,12 @@ def run_reference(args):
     g, S, T, K, spec = load_workload(0)
     import oracle
     oracle.build()
-    per_step = 16
+    # queries per step: about 0.4 s of oracle work, so that the whole run stays
+    # within a few minutes whatever --steps is
+    t0 = time.perf_counter()
+    oracle.topk_paths_batch(g, S[:4], T[:4], K)
+    rate = 4 / max(time.perf_counter() - t0, 1e-6)
+    per_step = int(min(16, max(1, round(0.4 * rate))))
     times = []
     qi = 0
     for step in range(args.warmup + args.steps):
@@ -239,7 +244,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": DATA,
             "config": {"workload": WORKLOAD_DESC, "queries_per_step": per_step,
-                       "note": "CPU oracle: fp64 brute force, OpenMP over queries, 16 queries per step"},
+                       "note": f"CPU oracle: fp64 brute force, OpenMP over queries, {per_step} queries per step"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": f"{per_step} queries per step cycling through the {len(S)} workload queries"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
