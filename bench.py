@@ -221,12 +221,8 @@ def run_reference(args):
     g, S, T, K, spec = load_workload(0)
     import oracle
     oracle.build()
-    # queries per step: about 0.4 s of oracle work, so that the whole run stays
-    # within a few minutes whatever --steps is
-    t0 = time.perf_counter()
-    oracle.topk_paths_batch(g, S[:4], T[:4], K)
-    rate = 4 / max(time.perf_counter() - t0, 1e-6)
-    per_step = int(min(16, max(1, round(0.4 * rate))))
+    # one query per oracle thread per step (the oracle runs queries in parallel)
+    per_step = max(1, min(len(S), oracle.num_threads()))
     times = []
     qi = 0
     for step in range(args.warmup + args.steps):
