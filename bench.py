@@ -71,6 +71,12 @@ FORM_DESC = {"plain": "plain: batched, every middle edge scored, fp32 screen + f
 # k_mlp_keys, k_order_hist, scan x2, k_order_perm, scan x2, k_near, k_middle (seed),
 # k_middle, k_merge1, k_rescore, k_merge2, k_exact
 KERNELS_PER_STEP = 22
+# DRAM bytes (read + write) of one main join launch from one ncu capture of the
+# current kernel (workload, form, work-item size, scan tile): 96,127,488 read +
+# 4,900,352 written, learned-ordered form on the medium workload, 16,384-edge
+# items, tile 4; the seed launch adds about 17 MB.  Kept only for that exact
+# configuration.
+TRAFFIC_NCU = {("medium", "chosen", 16384, 4): 101_027_840}
 
 
 def dist_env():
@@ -413,7 +419,9 @@ def run_gpu(args):
                     "d2h_bytes_per_step": nq * K * 24 + 4 * nq},
             "gpu_launches": KERNELS_PER_STEP * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": TRAFFIC_NCU.get((WORKLOAD, args.form, opts.get("chunk"), opts.get("tile"))),
+                         "traffic_scope": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the main join launch",
                          "kernel": "k_middle (middle join)", "peak_source": f"{peak_src} hbm_gbs",
                          "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": join_avg_ms,
                          "bytes_moved_per_launch": moved_bytes,
