@@ -741,6 +741,17 @@ __device__ void finish_query(MidSmem& sm, const PlanDev* __restrict__ P, int K) 
     __syncthreads();
 }
 
+// number of set bits of the far bitmap before bit b: the 256-bit block's rank,
+// whole 64-bit words of the block below b, the low half of b's 64-bit word when
+// b lies in its high half, then b's own word
+__device__ __forceinline__ uint32_t bm_rank(const MidSmem& sm, uint32_t b) {
+    const uint64_t* bm64 = reinterpret_cast<const uint64_t*>(sm.bm);
+    uint32_t r = sm.rank[b >> 8];
+    for (uint32_t w = (b >> 8) << 2; w < (b >> 6); ++w) r += __popcll(bm64[w]);
+    if (b & 32u) r += __popc(sm.bm[(b >> 5) - 1u]);
+    return r + __popc(sm.bm[b >> 5] & ((1u << (b & 31u)) - 1u));
+}
+
 __device__ void setup_query(MidSmem& sm, const PlanDev* __restrict__ P, int q) {
     if (threadIdx.x == 0) {
         sm.q = q;
@@ -769,7 +780,7 @@ __device__ void setup_query(MidSmem& sm, const PlanDev* __restrict__ P, int q) {
         atomicOr(&sm.bm[bv >> 5], 1u << (bv & 31u));
     }
     __syncthreads();
-    if (sigma == 0) {
+    {
         // rank[b] = set bits in words [0, 8b)
         const int nblk = (nbw + kRankWords - 1) / kRankWords;
         const int per = (nblk + blockDim.x - 1) / blockDim.x;  // <= 4
@@ -792,6 +803,17 @@ __device__ void setup_query(MidSmem& sm, const PlanDev* __restrict__ P, int q) {
         }
     }
     __syncthreads();
+    if (sigma > 0) {
+        // coarse bitmap (2^sigma vertices per bit): the far list is sorted by
+        // vertex, so the vertices of a set bit are contiguous in it; record
+        // where the run of each set bit starts, indexed by the bit's rank
+        uint32_t* fs = P->far_start + static_cast<int64_t>(blockIdx.x) * P->far_cap;
+        for (int k = threadIdx.x; k < sm.far_cnt; k += blockDim.x) {
+            const uint32_t bv = far[k].vertex >> sigma;
+            if (k == 0 || (far[k - 1].vertex >> sigma) != bv) fs[bm_rank(sm, bv)] = static_cast<uint32_t>(k);
+        }
+        __syncthreads();
+    }
 }
 
 __device__ __forceinline__ float4 ld4(const float* base, int64_t row, int d, int j) {
@@ -1302,6 +1324,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         const uint32_t* colsrc = sm.dir ? g.col : g.rcol;
         const ListEnt* far = P->list + sm.far_base;
         const int far_cnt = sm.far_cnt;
+        const uint32_t* far_start = P->far_start + static_cast<int64_t>(blockIdx.x) * P->far_cap;
         MHR_WSTART();
         for (int gb = warp * UNROLL; gb < ngroups; gb += kMidWarps * UNROLL) {
             MHR_SUB_START();
@@ -1383,24 +1406,15 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                     const uint32_t word = sm.bm[bv >> 5];
                     if ((word >> (bv & 31u)) & 1u) {
                         if (sigma == 0) {
-                            // set bits before x: the 256-bit block's rank, whole 64-bit
-                            // words of the block below x, the low half of x's 64-bit
-                            // word when x lies in its high half, then x's own word
-                            const uint64_t* bm64 = reinterpret_cast<const uint64_t*>(sm.bm);
-                            uint32_t r = sm.rank[x >> 8];
-                            for (uint32_t w = (x >> 8) << 2; w < (x >> 6); ++w) r += __popcll(bm64[w]);
-                            if (x & 32u) r += __popc(sm.bm[(x >> 5) - 1u]);
-                            fk = r + __popc(word & ((1u << (x & 31u)) - 1u));
+                            // exact bitmap: the rank of x is its far-list index
+                            fk = bm_rank(sm, x);
                             hit = true;
                         } else {
-                            int lo = 0, hi = far_cnt;
-                            while (lo < hi) {
-                                const int mid = (lo + hi) >> 1;
-                                if (far[mid].vertex < x) lo = mid + 1;
-                                else hi = mid;
-                            }
-                            if (lo < far_cnt && far[lo].vertex == x) {
-                                fk = static_cast<uint32_t>(lo);
+                            // coarse bitmap: walk the run of the set bit in the far list
+                            int k = static_cast<int>(far_start[bm_rank(sm, bv)]);
+                            while (k < far_cnt && far[k].vertex < x) ++k;
+                            if (k < far_cnt && far[k].vertex == x) {
+                                fk = static_cast<uint32_t>(k);
                                 hit = true;
                             }
                         }
@@ -2122,6 +2136,7 @@ struct Plan {
     void* slot_mem = nullptr;
     int64_t slot_cap = 0;
     void* item_mem = nullptr;
+    void* far_mem = nullptr;
     cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
     cudaStream_t cap = nullptr;
     cudaEvent_t h2d_done = nullptr;
@@ -2143,6 +2158,7 @@ struct Plan {
         for (void* p : fixed) cudaFree(p);
         if (slot_mem) cudaFree(slot_mem);
         if (item_mem) cudaFree(item_mem);
+        if (far_mem) cudaFree(far_mem);
         if (dregion) cudaFree(dregion);
         if (pin) cudaFreeHost(pin);
     }
@@ -2258,6 +2274,26 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
 // The sequence is captured as three graphs (before, the join, after) so that
 // timing events recorded between their launches on the caller's stream bracket
 // the join kernel exactly.
+// run starts of the coarse far bitmap, one array of `cap` per join CTA (only
+// graphs too large for the exact shared-memory bitmap need them)
+static mhr_status ensure_far(Plan* p, int64_t cap) {
+    if (p->h.sigma == 0) return MHR_OK;
+    cap = std::max<int64_t>(cap, 1);
+    if (cap <= p->h.far_cap && p->h.far_start) return MHR_OK;
+    cap = std::max(cap, 2 * p->h.far_cap);
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, sizeof(uint32_t) * static_cast<size_t>(cap) * p->grid);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (far-set run starts)");
+    if (p->far_mem) {
+        cudaDeviceSynchronize();
+        cudaFree(p->far_mem);
+    }
+    p->far_mem = mem;
+    p->h.far_start = static_cast<uint32_t*>(mem);
+    p->h.far_cap = cap;
+    return MHR_OK;
+}
+
 static mhr_status ensure_items(Plan* p, int64_t cap) {
     cap = std::max<int64_t>(cap, 1);
     if (cap <= p->h.item_cap && p->h.item_ub) return MHR_OK;
@@ -2558,6 +2594,10 @@ static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint
         icap += (bound + chunk - 1) / chunk;
     }
     MHR_TRY(ensure_items(p, icap));
+    // a far list is at most the row of s or the reverse row of t
+    int64_t fcap = 0;
+    for (int q = 0; q < nq; ++q) fcap = std::max(fcap, std::max(pa[q + 1] - pa[q], pc[q + 1] - pc[q]));
+    MHR_TRY(ensure_far(p, fcap));
     p->h.X = ta + tc;
     p->h.totA = ta;
     p->h.prune = (opts && opts->prune) ? 1 : 0;

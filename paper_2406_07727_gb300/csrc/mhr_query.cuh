@@ -143,6 +143,8 @@ struct PlanDev {
     unsigned long long* counters;  // kCntCount
     unsigned long long* cursors;   // [grid] next item of each CTA's own range
     uint32_t* drained;             // [(grid + 31) / 32] bit v: range v has no item left
+    uint32_t* far_start;           // [grid x far_cap] coarse bitmap: far-list start of each set bit's run
+    int64_t far_cap;               // longest far list of the batch (coarse bitmaps only)
     int64_t* partials;             // scan scratch
 };
 
