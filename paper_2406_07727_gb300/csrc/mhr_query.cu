@@ -8,22 +8,27 @@
 // a meet-in-the-middle join sized for one GB300:
 //
 //   expand   hop-1 row of s and hop-3 (reverse) row of t, fp32 weights,
-//            distinct frontier vertices with their best weight       (k_expand, k_lists)
-//   plan     per query: S_f = sum out-degrees over N_out(s), S_b = sum
-//            in-degrees over N_in(t); scan the smaller side; split the scan
-//            into work items of `chunk` CSR entries                  (k_plan, k_near)
-//   join     one persistent 1024-thread CTA per SM pops items from an atomic
-//            queue; the far frontier sits in a shared-memory bitmap (with a
-//            popcount rank, so the join needs no hash probe), the near rows are
-//            streamed warp-cooperatively, every hit is scored in fp32 and every
-//            path whose fp32 score can still reach the top K (within the proven
-//            fp32 error bound of the running K-th score) is kept in a
+//            distinct frontier vertices with their best weight; S_f = sum of
+//            out-degrees over N_out(s), S_b = sum of in-degrees over N_in(t)  (k_expand, k_lists)
+//   plan     per query: scan the smaller side; split the scan into work
+//            items of `chunk` CSR entries; order the near rows (natural, by
+//            their score bound, or by bound + learned slack) and describe
+//            every item                                               (k_plan, k_order_*, k_mlp_*, k_near)
+//   join     a seed launch does the first rows of every multi-item query, then
+//            one persistent 1024-thread CTA per SM takes items from its own
+//            range and steals from the others; the far frontier sits in a
+//            shared-memory bitmap (with a popcount rank, so the join needs no
+//            hash probe), the near rows are streamed warp-cooperatively, every
+//            hit whose bound can reach the kept band is scored in fp32 and
+//            every path whose fp32 score can still reach the top K (within the
+//            proven fp32 error bound of the running K-th score) is kept in a
 //            shared-memory buffer; radix select + compaction bound the buffer,
 //            and the CTA's K-th score is published with atomicMax      (k_middle)
 //   merge    per query: exact K-th fp32 score over the kept candidates, the
 //            band within twice the error bound, fp64 rescoring in the
-//            canonical order, bitonic sort by the total order          (k_merge1, k_rescore, k_merge2)
-//   exact    queries whose band is too dense for the fp32 screen (ties) are
+//            canonical order (each distinct edge once), bitonic sort by the
+//            total order                                             (k_merge1, k_rescore, k_merge2)
+//   exact    queries whose band overflows every buffer (ties) are
 //            recomputed with fp64 keys throughout                      (k_exact)
 //
 // Every kernel reads sizes and pointers from a device-resident PlanDev, so the
