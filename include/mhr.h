@@ -119,7 +119,8 @@ typedef struct {
     int32_t chunk;       /* edges per work item of the middle join: 0 = default (16384), else a
                             multiple of 32 in [32, 16384] (MHR_EINVAL otherwise) */
     int32_t order;       /* order of intermediate vertices: 0 natural, 1 by score
-                            bound, 2 by the learned score of `mlp` */
+                            bound, 2 by score bound refined inside bound levels by
+                            the learned slack prediction of `mlp` */
     int32_t prune;       /* 1 = skip work items, rows and middle edges whose provable
                             score bound cannot reach the kept band (same result) */
     int32_t precision;   /* middle-edge screen: 0 fp32 CUDA cores; 1 bf16 tensor-core

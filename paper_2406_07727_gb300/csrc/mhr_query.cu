@@ -404,14 +404,14 @@ __global__ void __launch_bounds__(kMlpHid) k_mlp_qbias(const PlanDev* __restrict
     }
 }
 
-// Learned order key of every near entry (order 2): the MLP predicts the best
-// completion of a path through the entry from [e_entry; e_far endpoint]; the
-// key adds the entry's own best hop weight.  Tiles of 32 slots.
+// Learned order (order 2): for every near entry the MLP predicts, from
+// [e_entry; e_far endpoint], the slack of its row bound (best path score
+// through the entry minus the bound); near_bucket orders the rows inside each
+// bound level by it.  Tiles of 32 slots.
 __global__ void __launch_bounds__(kMlpThreads) k_mlp_keys(const PlanDev* __restrict__ P, DevGraph g) {
     if (P->order != 2) return;
     __shared__ float part[kMlpRows][4];
     __shared__ uint32_t va[kMlpRows], vb[kMlpRows];
-    __shared__ float own[kMlpRows];
     __shared__ int64_t slot[kMlpRows];
     __shared__ int qrow[kMlpRows];
     const int nq = P->nq;
@@ -421,7 +421,6 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_keys(const PlanDev* __restr
             const int64_t r = t0 + threadIdx.x;
             slot[threadIdx.x] = -1;
             va[threadIdx.x] = vb[threadIdx.x] = 0u;
-            own[threadIdx.x] = 0.f;
             if (r < rows) {
                 const int q = static_cast<int>(upper_bound_i64(P->near_off, nq + 1, r) - 1);
                 const bool fwd = P->dir[q] == 1;
@@ -431,7 +430,6 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_keys(const PlanDev* __restr
                 slot[threadIdx.x] = x;
                 va[threadIdx.x] = e.vertex;
                 vb[threadIdx.x] = fwd ? P->T[q] : P->S[q];
-                own[threadIdx.x] = P->bnat[x];
                 qrow[threadIdx.x] = q;
             }
         }
@@ -441,21 +439,9 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_keys(const PlanDev* __restr
         auto bias = [&](int r, int c) -> float {
             return slot[r] >= 0 ? P->mlp_qbias[static_cast<int64_t>(qrow[r]) * kMlpHid + c] : 0.f;
         };
-        auto store_y = [&](int r, float y) {  // called by the 32 lanes of warp 0, row r = lane
-            uint32_t qid = 0xffffffffu, key = 0u;
-            if (slot[r] >= 0) {
-                // order key: the row bound plus the predicted (non-positive) slack
-                key = f2key(__fadd_rn(own[r], fminf(y, 0.f)));
-                P->mlp_pred[slot[r]] = key2f(key);
-                P->okey[slot[r]] = key;
-                qid = static_cast<uint32_t>(qrow[r]);
-            }
-            const unsigned peers = __match_any_sync(0xffffffffu, qid);
-            const uint32_t kmin = __reduce_min_sync(peers, key), kmax = __reduce_max_sync(peers, key);
-            if (qid != 0xffffffffu && r == __ffs(peers) - 1) {
-                atomicMin(&P->qkey[2 * qid], kmin);
-                atomicMax(&P->qkey[2 * qid + 1], kmax);
-            }
+        auto store_y = [&](int r, float y) {
+            // the predicted slack of the row bound (a path can only score below it)
+            if (slot[r] >= 0) P->mlp_pred[slot[r]] = fminf(y, 0.f);
         };
         auto store_z = [&](int, int, float) {};
         mlp_tile_k<kMlpIn / 32>(P->mlp, a_pair, bias, store_y, store_z, false, part);
@@ -488,7 +474,7 @@ __global__ void k_order_key(const PlanDev* __restrict__ P, DevGraph g) {
                 if (sideA) b = __fadd_rn(__fadd_rn(e.maxw, e.midw), key2f(P->qmax[2 * q + 1]));
                 else b = __fadd_rn(__fadd_rn(key2f(P->qmax[2 * q]), e.midw), e.maxw);
                 P->bnat[x] = b;
-                if (order == 1) {  // order 2 keys: k_mlp_keys
+                if (order != 0) {  // both orders sort by the bound first
                     key = f2key(b);
                     P->okey[x] = key;
                     qid = static_cast<uint32_t>(q);
@@ -504,10 +490,26 @@ __global__ void k_order_key(const PlanDev* __restrict__ P, DevGraph g) {
     }
 }
 
-// 256 buckets per query, highest keys first
-__device__ __forceinline__ uint32_t order_bucket(uint32_t key, uint32_t kmin, uint32_t kmax) {
+// `levels` buckets of the query's key range, highest keys first
+__device__ __forceinline__ uint32_t order_bucket(uint32_t key, uint32_t kmin, uint32_t kmax, uint32_t levels) {
     const uint64_t range = static_cast<uint64_t>(kmax - kmin) + 1;
-    return static_cast<uint32_t>((static_cast<uint64_t>(kmax - key) * 256) / range);
+    return static_cast<uint32_t>((static_cast<uint64_t>(kmax - key) * levels) / range);
+}
+
+// Bucket (0..255) of near entry x of query q.  Order 1: 256 levels of the row
+// bound.  Order 2: 64 levels of the row bound, each split in four by the
+// learned slack prediction counted in level widths (0, 1, 2, 3 or more), so
+// that within a bound level the rows predicted closest to their bound come
+// first while the items keep falling bounds, which lets whole items be skipped.
+__device__ __forceinline__ uint32_t near_bucket(const PlanDev* __restrict__ P, int64_t x, int q) {
+    const uint32_t kmin = P->qkey[2 * q], kmax = P->qkey[2 * q + 1];
+    if (P->order != 2) return order_bucket(P->okey[x], kmin, kmax, 256u);
+    const uint32_t lvl = order_bucket(P->okey[x], kmin, kmax, 64u);
+    const float width = (key2f(kmax) - key2f(kmin)) * (1.f / 64.f);
+    const float slack = -P->mlp_pred[x];  // >= 0, or NaN
+    uint32_t sub = 0u;
+    if (width > 0.f && slack > 0.f) sub = static_cast<uint32_t>(fminf(3.f, floorf(slack / width)));
+    return lvl * 4u + sub;
 }
 
 __global__ void k_order_hist(const PlanDev* __restrict__ P) {
@@ -519,7 +521,7 @@ __global__ void k_order_hist(const PlanDev* __restrict__ P) {
         int64_t base;
         bool sideA;
         if (!near_slot(P, x, q, base, sideA)) continue;
-        const uint32_t b = order_bucket(P->okey[x], P->qkey[2 * q], P->qkey[2 * q + 1]);
+        const uint32_t b = near_bucket(P, x, q);
         P->orank[x] = atomicAdd(&P->hist[static_cast<int64_t>(q) * 256 + b], 1u);
     }
 }
@@ -536,7 +538,7 @@ __global__ void k_order_perm(const PlanDev* __restrict__ P) {
         if (!near_slot(P, x, q, base, sideA)) continue;
         int64_t pos = x - base;
         if (order != 0) {
-            const uint32_t b = order_bucket(P->okey[x], P->qkey[2 * q], P->qkey[2 * q + 1]);
+            const uint32_t b = near_bucket(P, x, q);
             const int64_t h = static_cast<int64_t>(q) * 256;
             pos = P->hscan[h + b] - P->hscan[h] + P->orank[x];
         }

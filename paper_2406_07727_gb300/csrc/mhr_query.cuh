@@ -105,7 +105,7 @@ struct PlanDev {
     uint32_t* nperm;    // ordered position -> dense index of the near entry
     uint32_t* degv3;    // scan degree in ordered position
     int64_t* scan4;     // prefix of degv3
-    float* mlp_pred;    // learned order key (order 2)
+    float* mlp_pred;    // order 2: predicted slack (<= 0) of each near entry's row bound
     uint32_t* ubest;    // label dump: key of the best fp32 path through a near entry (ordered position)
     double* w64s;       // fp64 weight of a hop-1 / hop-3 slot used by the band
     int32_t* w64own;    // 1 once a band entry has claimed the slot's fp64 sum

@@ -5,9 +5,10 @@ e_endpoint[0:128]] -> 256 ReLU units -> 1).  It is trained to predict the
 slack of the search's provable row bound for an intermediate vertex x: the
 best fp32 path score through x minus that bound, both produced by plain
 (exact, unpruned) runs of the search (``mhr_training_labels``).  At query
-time the library orders the rows it scans by bound + min(0, prediction), so
-the K-th score of a query rises early; pruning stays bound-based, so results
-never change.
+time the library sorts the rows it scans into 64 levels of their bound and,
+inside a level, by the predicted slack (rows predicted closest to their bound
+first), so the K-th score of a query rises early while whole work items can
+still be skipped; pruning stays bound-based, so results never change.
 
 This module only drives: data movement, shuffling and the epoch loop run on
 the host; labels, features, forward, backward and Adam run in the library's
