@@ -318,6 +318,7 @@ def run_gpu(args):
                                           opts=o, with_stats=with_stats)
 
     dense_steps = []
+    spreads = []
 
     def timed(o, steps, sampler=None):
         for _ in range(args.warmup):
@@ -331,19 +332,27 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if sampler:
             sampler.start()
+        # timed steps: no statistics read-back inside the timed region (it
+        # synchronises after every step and is not part of the work)
         for i in range(steps):
             flush.zero_()
             ev[i][0].record(stream)
-            _, _, st = step(o, with_stats=True)
+            step(o)
             ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        clk = sampler.stop() if sampler else None
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        el = max_over_ranks(sum(step_ms), ws, "cuda")
+        if ws > 1:
+            dist.barrier()
+        # the library's own counters and event times, from untimed steps of the same work
+        for _ in range(min(steps, 10)):
+            flush.zero_()
+            _, _, st = step(o, with_stats=True)
             join_ms.append(st["ms_join"])
             dev_ms.append(st["ms_device"])
             dense_steps.append(st["dense_queries"])
-        torch.cuda.synchronize()
-        clk = sampler.stop() if sampler else None
-        el = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), ws, "cuda")
-        if ws > 1:
-            dist.barrier()
+        spreads.append(step_ms)
         return el, join_ms, dev_ms, st, clk
 
     clocks = ClockSampler(local)
@@ -438,9 +447,13 @@ def run_gpu(args):
                                "loss_first": train_rep.loss_first, "loss_last": train_rep.loss_last,
                                "train_s": train_s} if train_rep else None),
             "device_ms_per_step": statistics.mean(dev_ms),
+            "step_ms_spread": {"min": min(spreads[0]), "median": statistics.median(spreads[0]),
+                               "max": max(spreads[0])},
             "device_ms_spread": {"min": min(dev_ms), "median": statistics.median(dev_ms), "max": max(dev_ms)},
             "join_ms_spread": {"min": min(join_ms), "median": statistics.median(join_ms), "max": max(join_ms)},
             "steps_with_dense_queries": sum(1 for x in dense_steps if x),
+            "stats_steps": "work counters, device/join times and dense counts come from up to 10 untimed "
+                           "steps of the same work after the timed loop",
             "device_host_agree": agree,
             "wall_s_timed_loop": wall1 - wall0,
         }
