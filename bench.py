@@ -72,11 +72,11 @@ FORM_DESC = {"plain": "plain: batched, every middle edge scored, fp32 screen + f
 # k_middle, k_merge1, k_rescore, k_merge2, k_exact
 KERNELS_PER_STEP = 22
 # DRAM bytes (read + write) of one main join launch from one ncu capture of the
-# current kernel (workload, form, work-item size, scan tile): 96,511,744 read +
-# 5,068,800 written, learned-ordered form on the medium workload, 16,384-edge
+# current kernel (workload, form, work-item size, scan tile): 94,522,368 read +
+# 4,869,632 written, learned-ordered form on the medium workload, 16,384-edge
 # items, tile 4; the seed launch adds about 17 MB.  Kept only for that exact
 # configuration.
-TRAFFIC_NCU = {("medium", "chosen", 16384, 4): 101_580_544}
+TRAFFIC_NCU = {("medium", "chosen", 16384, 4): 99_392_000}
 
 
 def dist_env():
