@@ -352,7 +352,7 @@ def workload(name: str, seed: int = 0, **override):
     g, S, T, K, spec = _build_workload(spec, seed)
     if cp is not None:
         import os
-        tmp = cp + ".tmp.npz"
+        tmp = f"{cp}.{os.getpid()}.tmp.npz"  # one writer per file; the rename is atomic
         try:
             np.savez(tmp, offsets=g.offsets, cols=g.cols, rels=g.rels, vtypes=g.vtypes, vemb=g.vemb,
                      remb=g.remb, S=S, T=T)
