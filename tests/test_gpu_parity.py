@@ -222,14 +222,42 @@ def test_both_directions_and_repeat_determinism(mhr):
 
 
 def test_large_vertex_count_coarse_bitmap(mhr):
-    """n > 2^20: the shared-memory membership bitmap becomes coarse and
-    positives are confirmed by binary search."""
+    """n > 2^20: the shared-memory membership bitmap becomes coarse (several
+    vertices per bit); a positive is found in the run of its bit in the sorted
+    far list, located by the bit's rank.  Small work items exercise items and
+    seed parts that start inside a run."""
     g = synth.gen_rmat_kg(22, 3_000_000, 2_000_000, 4, 2, seed=6)
     g.vemb, g.remb = synth.gen_embeddings(g.n, g.R, 8, 0.3, seed=6)
     S, T = synth.queries_edge_biased(g, 24, seed=6)
     run_and_compare(mhr, g, S, T, 50, "transe")
     run_and_compare(mhr, g, S, T, 50, "transe", opts={"prune": 1})
     run_and_compare(mhr, g, S, T, 50, "transe", opts={"prune": 1, "order": 1})
+    run_and_compare(mhr, g, S, T, 50, "transe", opts={"prune": 1, "order": 1, "chunk": 256})
+
+
+def test_coarse_bitmap_dense_runs(mhr):
+    """A coarse bitmap whose set bits cover runs of several far vertices: a
+    hub target whose in-neighbours are consecutive vertex ids."""
+    rng = np.random.default_rng(12)
+    n, R = 2_200_000, 3
+    hub_t, hub_s = 1_000_003, 17
+    u = [hub_s] * 400
+    v = list(range(2_000, 2_400))                        # hop-1: consecutive u
+    r = list(rng.integers(0, R, 400))
+    mids = rng.integers(2_000, 2_400, 6_000)
+    for a, b in zip(mids, rng.integers(500_000, 500_600, 6_000)):
+        u.append(int(a)); v.append(int(b)); r.append(int(rng.integers(0, R)))   # middle edges
+    for b in range(500_000, 500_600):
+        u.append(b); v.append(hub_t); r.append(int(rng.integers(0, R)))          # hop-3: consecutive v
+    offsets, cols, rels = synth.canonicalize(n, R, np.array(u), np.array(r), np.array(v))
+    vemb = (rng.standard_normal((n, 8)) * 0.3).astype(np.float32)
+    remb = (rng.standard_normal((R, 8)) * 0.3).astype(np.float32)
+    g = synth.KG(n=n, R=R, n_types=1, offsets=offsets, cols=cols, rels=rels,
+                 vtypes=np.zeros(n, dtype=np.uint8), vemb=vemb, remb=remb, dtype="f32")
+    S = np.array([hub_s, hub_s], dtype=np.uint32)
+    T = np.array([hub_t, 500_010], dtype=np.uint32)
+    for o in (None, {"prune": 1, "order": 1}, {"prune": 1, "order": 1, "chunk": 64}):
+        run_and_compare(mhr, g, S, T, 40, "transe", opts=o)
 
 
 def test_device_memory_batched(mhr):
