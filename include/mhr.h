@@ -27,6 +27,9 @@
  *   - cuda_stream is a cudaStream_t (NULL = the legacy default stream).
  *   - The device is the one current on the calling thread when the graph is
  *     loaded; later calls on that graph must use the same device.
+ *   - A graph handle keeps per-shape query plans (buffers and captured CUDA
+ *     graphs); calls on one handle must not run concurrently from several
+ *     host threads.  Different handles are independent.
  */
 #ifndef MHR_H
 #define MHR_H
