@@ -7,7 +7,9 @@ the CUDA package never imports it.
 Two independent routes compute the same result:
   * ``mhr_oracle.c`` (brute force, fp64, canonical operation order) through
     ctypes: ``edge_weights``, ``topk_paths``, ``topk_paths_batch``,
-    ``query_stats``;
+    ``query_stats``, and the tail-prediction scan of Alg. 3 / Alg. 4,
+    ``tail_topk`` (every candidate vertex of one type scored against a
+    (head, relation) pair, the K best kept);
   * ``mitm.py``: a pure-Python meet-in-the-middle enumeration with its own
     edge-weight loop, used to cross-check the brute force on small graphs.
 """
@@ -35,6 +37,7 @@ BF16 = 1
 
 PATH_DTYPE = np.dtype([("score", "<f8"), ("u", "<u4"), ("v", "<u4"),
                        ("r1", "<u2"), ("r2", "<u2"), ("r3", "<u2"), ("pad", "<u2")])
+TAIL_DTYPE = np.dtype([("score", "<f8"), ("v", "<u4"), ("pad", "<u4")])
 STATS_DTYPE = np.dtype([(k, "<i8") for k in
                         ("deg_s", "deg_t", "n_u", "n_v", "s_f", "s_b", "hits", "paths")])
 
@@ -75,6 +78,9 @@ def _load():
                                                 i64, P, P, P]
         lib.oracle_query_stats.restype = i32
         lib.oracle_query_stats.argtypes = [P, P, i64, u32, u32, P]
+        lib.oracle_tail_topk_batch.restype = i32
+        lib.oracle_tail_topk_batch.argtypes = [P, i64, i64, P, P, i32, i32, i32, f64, i64, P, P,
+                                               i32, i64, P, P, P]
         lib.oracle_num_threads.restype = i32
         lib.oracle_num_threads.argtypes = []
         _lib = lib
@@ -156,6 +162,30 @@ def topk_paths_batch(g, S, T, K: int, fn="transe", gamma=1.0):
                                      _ptr(n_out), _ptr(status))
     if rc:
         raise ValueError(f"oracle batch failed on queries {np.flatnonzero(status).tolist()[:8]}")
+    return out, n_out
+
+
+def tail_topk(g, H, Rq, K: int, cand_type: int = -1, fn="transe", gamma=1.0):
+    """Tail prediction (Alg. 3 / Alg. 4) for the queries (H[i], Rq[i]): the K
+    best candidates c (vtypes[c] == cand_type, or all vertices when
+    cand_type < 0) by w(H[i], Rq[i], c).  Returns (out [nq, K] of TAIL_DTYPE,
+    n_out [nq])."""
+    lib = _load()
+    G = _G(g)
+    vt = np.ascontiguousarray(g.vtypes, dtype=np.uint8)
+    H = np.ascontiguousarray(H, dtype=np.uint32)
+    Rq = np.ascontiguousarray(Rq, dtype=np.uint32)
+    nq = H.shape[0]
+    out = np.zeros((nq, max(int(K), 1)), dtype=TAIL_DTYPE)
+    n_out = np.zeros(nq, dtype=np.int64)
+    status = np.zeros(nq, dtype=np.int32)
+    rc = lib.oracle_tail_topk_batch(_ptr(vt), G.n, int(g.R), _ptr(G.vemb), _ptr(G.remb), G.dtype, G.d,
+                                    FN_CODES[fn], float(gamma), nq, _ptr(H), _ptr(Rq), int(cand_type),
+                                    int(K), _ptr(out), _ptr(n_out), _ptr(status))
+    if rc == 1:
+        raise ValueError("invalid tail query (head or relation out of range, or K <= 0)")
+    if rc:
+        raise RuntimeError(f"oracle_tail_topk_batch: {rc}")
     return out, n_out
 
 

@@ -28,6 +28,10 @@
  *   keep only the K highest scores; the "MaxHeap" of Alg. 3/4 is read as the
  *   structure that keeps the K highest scores, evicting the lowest].
  *
+ * Tail prediction (Alg. 3, Alg. 4): oracle_tail_topk below scores every
+ * candidate vertex of one type against one (head, relation) pair with the same
+ * edge weight and keeps the K best (score descending, then vertex ascending).
+ *
  * Parity pins (tests/): hand-derived examples with dyadic embeddings, closed
  * forms (zero embeddings), the exact rational edge weight within the fp64
  * rounding bound, an independent meet-in-the-middle route in pure Python,
@@ -246,6 +250,71 @@ int oracle_topk_paths_batch(const int64_t* offsets, const uint32_t* cols, const 
     for (int64_t q = 0; q < nq; ++q) {
         int st = oracle_topk_paths(offsets, cols, rels, n, vemb, remb, dtype, d, fn, gamma, S[q],
                                    T[q], K, out + q * K, &n_out[q], NULL, NULL);
+        status[q] = st;
+        if (st != ORACLE_OK) {
+#pragma omp atomic write
+            any = st;
+        }
+    }
+    return any;
+}
+
+/* ------------------------------------------------------------------------ */
+/*
+ * Tail prediction [Alg. 3 scores every person against the aggregated
+ * Turing-award embedding; Alg. 4 scores every university for one person]:
+ * for a head h and a relation r, every candidate vertex c -- the vertices
+ * with vtypes[c] == cand_type, or all vertices when cand_type < 0 -- gets the
+ * edge weight w(h, r, c) above, and the K best are kept in the order score
+ * descending, then c ascending.  The paper's loops skip no candidate, so the
+ * head is a candidate too when its type matches.  The bounded heap of the
+ * path search is reused with the candidate in the u field and zero relation
+ * fields, which makes its order (score desc, u asc) exactly this order.
+ */
+typedef struct {
+    double score;
+    uint32_t v;
+    uint32_t pad;
+} oracle_tail;                      /* 16 bytes, same layout as the library's */
+
+int oracle_tail_topk(const uint8_t* vtypes, int64_t n, int64_t R, const void* vemb,
+                     const void* remb, int dtype, int d, int fn, double gamma, uint32_t h,
+                     uint32_t r, int cand_type, int64_t K, oracle_tail* out, int64_t* n_out) {
+    if ((int64_t)h >= n || (int64_t)r >= R || K <= 0) return ORACLE_EINVAL;
+    khe hp;
+    hp.a = (oracle_path*)malloc(sizeof(oracle_path) * (size_t)K);
+    if (!hp.a) return ORACLE_ENOMEM;
+    hp.size = 0;
+    hp.cap = K;
+    for (int64_t c = 0; c < n; ++c) {
+        if (cand_type >= 0 && (int)vtypes[c] != cand_type) continue;
+        oracle_path p;
+        memset(&p, 0, sizeof p);
+        p.score = oracle_edge_weight(vemb, remb, dtype, d, fn, gamma, h, r, (uint32_t)c);
+        p.u = (uint32_t)c;
+        khe_push(&hp, &p);
+    }
+    qsort(hp.a, (size_t)hp.size, sizeof(oracle_path), cmp_rank);
+    for (int64_t i = 0; i < hp.size; ++i) {
+        out[i].score = hp.a[i].score;
+        out[i].v = hp.a[i].u;
+        out[i].pad = 0;
+    }
+    *n_out = hp.size;
+    free(hp.a);
+    return ORACLE_OK;
+}
+
+/* Many tail queries (H[q], Rq[q]), in parallel over queries. */
+int oracle_tail_topk_batch(const uint8_t* vtypes, int64_t n, int64_t R, const void* vemb,
+                           const void* remb, int dtype, int d, int fn, double gamma, int64_t nq,
+                           const uint32_t* H, const uint32_t* Rq, int cand_type, int64_t K,
+                           oracle_tail* out, int64_t* n_out, int32_t* status) {
+    int any = ORACLE_OK;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < nq; ++q) {
+        int st = oracle_tail_topk(vtypes, n, R, vemb, remb, dtype, d, fn, gamma, H[q], Rq[q],
+                                  cand_type, K, out + q * K, &n_out[q]);
         status[q] = st;
         if (st != ORACLE_OK) {
 #pragma omp atomic write
