@@ -290,6 +290,50 @@ mhr_status mhr_mlp_to_bf16(const float* src, uint16_t* dst, int64_t count, void*
 mhr_status mhr_topk_paths_noalloc(const mhr_graph* g, uint32_t s, uint32_t t, int32_t K, mhr_path* out,
                                   int32_t* n_out, void* cuda_stream);
 
+/*
+ * Tail prediction (Alg. 3 and Alg. 4): Alg. 3 scores every person against the
+ * Turing-award embedding aggregated with the award-winner relation, Alg. 4
+ * every university against one person and the affiliation relation; both
+ * keep the K best with per-thread heaps merged by a tree (Alg. 2).  Here, for
+ * each query i, every candidate vertex c -- the vertices with
+ * vtypes[c] == cand_type, or every vertex when cand_type == -1 -- is scored
+ * with the graph's edge weight w(h[i], r[i], c) (no edge needs to exist), and
+ * the K best are returned in the order score descending, then c ascending
+ * (a total order, so the result is unique).  The head itself is a candidate
+ * when its type matches: the paper's loops exclude no candidate.  Scores are
+ * screened in fp32 with the graph's proven error bound and the boundary
+ * candidates are rescored in fp64 in the canonical operation order, so
+ * results are bit-identical to an fp64 brute force.
+ *   h, r      nq heads (< n_vertices) and relations (< n_relations)
+ *   out       nq*K records (query i at out[i*K]); n_out[i] = records written,
+ *             min(K, number of candidates)
+ *   mem       where h, r, out and n_out live (host or device)
+ *   stats     optional (host): edges_scanned = (query, candidate) pairs scored
+ *             in fp32 (the sampling pass included), candidates = fp32
+ *             survivors of the threshold, rescored = candidates rescored in
+ *             fp64, dense_queries = queries whose survivors overflowed the
+ *             sized buffer and were rescanned alone, ms = wall time,
+ *             ms_device = device time of the call, ms_join = device time of
+ *             the full scans; hits, paths and pruned_edges are 0.
+ * Synchronous.  MHR_EINVAL: NULL pointers, a head or relation out of range,
+ * cand_type outside [-1, 255], K < 1; MHR_ERANGE: K > MHR_TAIL_K_MAX or
+ * dim > 16383.  nq == 0 is a no-op.  The first query of a vertex type builds
+ * and keeps that type's candidate list on the device (4 bytes per vertex of
+ * the type, freed with the graph).
+ */
+#define MHR_TAIL_K_MAX 4096
+
+/* One tail-prediction result: candidate v with its fp64 score.  16 bytes. */
+typedef struct {
+    double score;
+    uint32_t v;
+    uint32_t pad;
+} mhr_tail;
+
+mhr_status mhr_tail_topk(const mhr_graph* g, int32_t nq, const uint32_t* h, const uint16_t* r,
+                         int32_t cand_type, int32_t K, mhr_tail* out, int32_t* n_out, mhr_mem mem,
+                         mhr_stats* stats, void* cuda_stream);
+
 /* Thread-local description of the last non-OK status ("" if none). */
 const char* mhr_last_error(void);
 

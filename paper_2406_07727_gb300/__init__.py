@@ -11,7 +11,9 @@ from ._mhr import (  # noqa: F401
     Graph,
     MhrError,
     PATH_DTYPE,
+    TAIL_DTYPE,
     MHR_K_MAX,
+    MHR_TAIL_K_MAX,
     MHR_OK,
     MHR_EINVAL,
     MHR_ENOMEM,
@@ -42,6 +44,8 @@ from ._mhr import (  # noqa: F401
     MLP,
     mhr_version,
     paths_from_device,
+    mhr_tail_topk,
+    tails_from_device,
 )
 
 from .learn import OrderingMLP, train_ordering_mlp  # noqa: E402,F401

@@ -31,6 +31,9 @@ SCORE_FNS = {"transe": MHR_SCORE_TRANSE_L1, "transe_l1": MHR_SCORE_TRANSE_L1,
 PATH_DTYPE = np.dtype([("score", "<f8"), ("u", "<u4"), ("v", "<u4"),
                        ("r1", "<u2"), ("r2", "<u2"), ("r3", "<u2"), ("pad", "<u2")])
 assert PATH_DTYPE.itemsize == 24
+TAIL_DTYPE = np.dtype([("score", "<f8"), ("v", "<u4"), ("pad", "<u4")])
+assert TAIL_DTYPE.itemsize == 16
+MHR_TAIL_K_MAX = 4096
 
 
 class MhrError(RuntimeError):
@@ -75,7 +78,7 @@ class Stats(ctypes.Structure):
 EXPORTS = ("mhr_graph_load", "mhr_graph_free", "mhr_edge_scores", "mhr_topk_paths",
            "mhr_topk_paths_batched", "mhr_topk_paths_noalloc", "mhr_training_labels",
            "mhr_mlp_features", "mhr_mlp_forward", "mhr_mlp_backward", "mhr_mlp_adam",
-           "mhr_mlp_to_bf16", "mhr_last_error", "mhr_version")
+           "mhr_mlp_to_bf16", "mhr_tail_topk", "mhr_last_error", "mhr_version")
 
 _lock = threading.Lock()
 _lib = None
@@ -129,6 +132,8 @@ def load_library(build_if_missing: bool = True):
         lib.mhr_mlp_to_bf16.argtypes = [P, P, i64, P]
         lib.mhr_topk_paths_noalloc.restype = ctypes.c_int
         lib.mhr_topk_paths_noalloc.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, i32, P, P, P]
+        lib.mhr_tail_topk.restype = ctypes.c_int
+        lib.mhr_tail_topk.argtypes = [P, i32, P, P, i32, i32, P, P, ctypes.c_int, ctypes.POINTER(Stats), P]
         lib.mhr_last_error.restype = ctypes.c_char_p
         lib.mhr_last_error.argtypes = []
         lib.mhr_version.restype = ctypes.c_char_p
@@ -369,6 +374,44 @@ def mhr_topk_paths_noalloc(g: Graph, s: int, t: int, K: int, out, n_out, stream=
         raise ValueError("out and n_out must be device tensors")
     _check(lib.mhr_topk_paths_noalloc(g.handle, ctypes.c_uint32(int(s)), ctypes.c_uint32(int(t)), int(K),
                                       _ptr(out), _ptr(n_out), _stream_ptr(stream)))
+
+
+def mhr_tail_topk(g: Graph, H, Rq, K: int, cand_type: int = -1, out=None, n_out=None, stream=None,
+                  with_stats: bool = False):
+    """Tail prediction (Alg. 3 / Alg. 4): for each query (H[i], Rq[i]) the K
+    best candidate vertices (vtypes == cand_type, or all when cand_type is -1)
+    by the edge weight w(H[i], Rq[i], c).  Host arrays in -> host arrays out
+    (out [nq, K] of TAIL_DTYPE); device tensors in -> device tensors out (a
+    uint8 tensor [nq, K*16]).  Synchronous."""
+    lib = load_library()
+    mem = _mem_of(H, Rq, out, n_out)
+    nq = int(H.shape[0])
+    if mem == MHR_MEM_HOST:
+        H, Rq = _host(H, np.uint32), _host(Rq, np.uint16)
+        if out is None:
+            out = np.zeros((nq, max(int(K), 1)), dtype=TAIL_DTYPE)
+        if n_out is None:
+            n_out = np.zeros(nq, dtype=np.int32)
+    else:
+        import torch
+        if out is None:
+            out = torch.empty((nq, max(int(K), 1) * TAIL_DTYPE.itemsize), dtype=torch.uint8, device=H.device)
+        if n_out is None:
+            n_out = torch.empty(nq, dtype=torch.int32, device=H.device)
+    st = Stats()
+    _check(lib.mhr_tail_topk(g.handle, nq, _ptr(H), _ptr(Rq), int(cand_type), int(K), _ptr(out), _ptr(n_out),
+                             mem, ctypes.byref(st) if with_stats else None, _stream_ptr(stream)))
+    if with_stats:
+        return out, n_out, st.as_dict()
+    return out, n_out
+
+
+def tails_from_device(buf, K: int) -> np.ndarray:
+    """uint8 device/host buffer [nq, K*16] -> structured numpy array [nq, K]."""
+    if hasattr(buf, "cpu"):
+        buf = buf.cpu().numpy()
+    buf = np.ascontiguousarray(buf)
+    return buf.view(TAIL_DTYPE).reshape(buf.shape[0], K)
 
 
 # --------------------------------------------------------------------------- learned ordering

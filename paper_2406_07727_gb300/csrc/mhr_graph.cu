@@ -545,12 +545,14 @@ void free_graph(mhr_graph* g);
 
 namespace mhr {
 void destroy_plans(mhr_graph* g);  // mhr_query.cu
+void destroy_tail(mhr_graph* g);   // mhr_tail.cu
 }
 
 namespace {
 void free_graph(mhr_graph* g) {
     if (!g) return;
     mhr::destroy_plans(g);
+    mhr::destroy_tail(g);
     for (void* p : g->allocations) cudaFree(p);
     delete g;
 }

@@ -62,6 +62,7 @@ struct DevBuf {
 };
 
 struct PlanCache;  // batched-query plans, defined in mhr_query.cu
+struct TailCache;  // tail-prediction candidate lists and scratch, defined in mhr_tail.cu
 
 }  // namespace mhr
 
@@ -84,6 +85,7 @@ struct mhr_graph {
     double max_l1 = 0, max_rel_l1 = 0, max_rel_inf = 0, max_l2sq = 0;
     int num_sms = 0;
     mhr::PlanCache* plans = nullptr;
+    mhr::TailCache* tail = nullptr;
 };
 
 namespace mhr {

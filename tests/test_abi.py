@@ -19,7 +19,7 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for want in ("mhr_graph_load", "mhr_graph_free", "mhr_edge_scores", "mhr_topk_paths",
-                 "mhr_topk_paths_batched", "mhr_last_error"):
+                 "mhr_topk_paths_batched", "mhr_tail_topk", "mhr_last_error"):
         assert want in names
 
 
@@ -41,6 +41,7 @@ def test_struct_layouts():
     import paper_2406_07727_gb300 as m
     from paper_2406_07727_gb300 import _mhr
     assert m.PATH_DTYPE.itemsize == 24
+    assert m.TAIL_DTYPE.itemsize == 16
     assert ctypes.sizeof(_mhr.GraphDesc) == 104
     assert ctypes.sizeof(_mhr.QueryOpts) == 32
     assert ctypes.sizeof(_mhr.Stats) == 80
@@ -61,4 +62,6 @@ def test_host_side_argument_checks():
     assert lib.mhr_graph_load(ctypes.byref(d), ctypes.byref(h), None) == m.MHR_EINVAL
     assert "n_relations" in m.mhr_last_error()
     assert h.value is None
+    assert lib.mhr_tail_topk(None, 1, None, None, -1, 5, None, None, 0, None, None) == m.MHR_EINVAL
+    assert "NULL" in m.mhr_last_error()
     assert m.mhr_version().startswith("mhr-gb300")
