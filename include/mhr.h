@@ -18,6 +18,9 @@
  * bound and the boundary candidates are rescored in fp64 in a fixed operation
  * order, so scores and order equal an fp64 brute-force enumeration
  * (j = 0..d-1 in order, no fused multiply-add).
+ * The library also provides the tail-prediction scan of Alg. 3 / Alg. 4
+ * (mhr_tail_topk): the K best candidate vertices of one type for
+ * (head, relation) queries, exact in the same way.
  *
  * Conventions for every entry point:
  *   - Status codes are returned, never raised; mhr_last_error() gives a

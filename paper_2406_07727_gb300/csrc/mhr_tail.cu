@@ -12,14 +12,16 @@
 //      per-edge error bound is a threshold that can drop no candidate of the
 //      exact top K (the K-th best of a subset is at most the K-th best of all);
 //   3. full pass (k_tail_scan): every candidate row is read once with 16-byte
-//      loads, a group of G lanes holding one row in registers, and scored
+//      loads, a group of G lanes holding two rows in registers, and scored
 //      against every query of the batch (query vectors e_h + w_r or
-//      e_h * w_r in shared memory); scores at or above the threshold are
-//      appended to the query's survivor list (warp-aggregated atomics);
+//      e_h * w_r in shared memory, each load feeding both rows); scores at or
+//      above the threshold are appended to the query's survivor list
+//      (warp-aggregated atomics);
 //   4. per query (k_tail_final): the exact K-th best fp32 survivor score by a
 //      radix select, the band of survivors within twice the error bound of it
-//      rescored in fp64 in the canonical operation order, and the K best of
-//      the band sorted in shared memory.
+//      rescored in fp64 in the canonical operation order (one member per
+//      thread, e_h + w_r formed once in fp64 in shared memory), and the K best
+//      of the band sorted in shared memory.
 //
 // Exactness: |S32 - w64| <= E = eps32 + eps64 for every candidate (the bound of
 // mhr_graph.cu holds for any (u, r, v) triple and any summation order).  If c
@@ -175,11 +177,53 @@ __device__ __forceinline__ void append(const ScanArgs& a, int qi, bool keep, flo
 }
 
 // ---------------------------------------------------------------------------
-// scan, 16-byte rows: a group of G lanes holds one candidate row in registers
-// (lane s of the group: 16-byte vectors s, s + G, ..., NV of them), so the
-// group's loads of one step are G consecutive vectors of the row.  EV
-// elements per vector (4 fp32 or 8 bf16).
+// scan, 16-byte rows: a group of G lanes holds two adjacent candidate rows in
+// registers (lane s of the group: 16-byte vectors s, s + G, ..., NV of them per
+// row), so the group's loads of one step are G consecutive vectors of a row,
+// and every query vector load from shared memory feeds both rows.  EV elements
+// per vector (4 fp32 or 8 bf16).
 // ---------------------------------------------------------------------------
+template <bool BF16>
+__device__ __forceinline__ void unpack_row(const uint4& w, float* x) {
+    if constexpr (BF16) {
+        x[0] = bf_lo(w.x);
+        x[1] = bf_hi(w.x);
+        x[2] = bf_lo(w.y);
+        x[3] = bf_hi(w.y);
+        x[4] = bf_lo(w.z);
+        x[5] = bf_hi(w.z);
+        x[6] = bf_lo(w.w);
+        x[7] = bf_hi(w.w);
+    } else {
+        x[0] = __uint_as_float(w.x);
+        x[1] = __uint_as_float(w.y);
+        x[2] = __uint_as_float(w.z);
+        x[3] = __uint_as_float(w.w);
+    }
+}
+
+template <bool TRANSE>
+__device__ __forceinline__ float term32(float q, float c) {
+    if constexpr (TRANSE) return fabsf(__fsub_rn(q, c));
+    else return q * c;
+}
+
+// keep-every-score mode (no threshold): candidate i of the visit order owns
+// slot i, no counter needed; otherwise a warp-aggregated append
+__device__ __forceinline__ void emit(const ScanArgs& a, int qi, bool valid, bool leader, float s32, uint32_t v,
+                                     int64_t i, int lane, float thr) {
+    if (a.thr == nullptr) {
+        if (valid && leader) a.surv[static_cast<int64_t>(qi) * a.cap + i] = SurvRec{s32, v};
+    } else {
+        append(a, qi, valid && leader && s32 >= thr, s32, v, lane);
+    }
+}
+
+__device__ __forceinline__ void keep_all_counts(const ScanArgs& a) {
+    if (a.thr == nullptr && blockIdx.x == 0)
+        for (int qi = threadIdx.x; qi < a.nq; qi += blockDim.x) a.cnt[qi] = static_cast<unsigned>(a.n_visit);
+}
+
 template <int NV, bool BF16, bool TRANSE>
 __global__ void __launch_bounds__(kScanThreads) k_tail_scan(ScanArgs a) {
     extern __shared__ float4 smem4[];
@@ -187,6 +231,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tail_scan(ScanArgs a) {
     const int d = a.g.d, nq = a.nq;
     float* sthr = sq + static_cast<int64_t>(nq) * d;
     load_queries(a, sq, sthr);
+    keep_all_counts(a);
 
     constexpr int EV = BF16 ? 8 : 4;
     const int dv = d / EV;
@@ -194,46 +239,33 @@ __global__ void __launch_bounds__(kScanThreads) k_tail_scan(ScanArgs a) {
     const int lane = threadIdx.x & 31;
     const int s = lane & (G - 1);
     const int grp = lane / G;
-    const int cpw = 32 / G;
+    const int cpw = 2 * (32 / G);
     const int64_t ntiles = (a.n_visit + cpw - 1) / cpw;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * kScanWarps;
     const size_t row_bytes = static_cast<size_t>(d) * (BF16 ? 2 : 4);
     const float gamma32 = a.g.gamma32;
 
     for (int64_t t = static_cast<int64_t>(blockIdx.x) * kScanWarps + (threadIdx.x >> 5); t < ntiles; t += nwarps) {
-        const int64_t i = t * cpw + grp;
-        const bool valid = i < a.n_visit;
-        uint32_t v = 0;
-        if (valid) {
-            const int64_t pos = i * a.stride;
-            v = a.cand ? __ldg(a.cand + pos) : static_cast<uint32_t>(pos);
-        }
-        const uint4* row = reinterpret_cast<const uint4*>(static_cast<const char*>(a.g.vemb) + v * row_bytes);
-        float x[NV * EV];
+        const int64_t i0 = t * cpw + 2 * grp, i1 = i0 + 1;
+        const bool valid0 = i0 < a.n_visit, valid1 = i1 < a.n_visit;
+        uint32_t v0 = 0, v1 = 0;
+        if (valid0) v0 = a.cand ? __ldg(a.cand + i0 * a.stride) : static_cast<uint32_t>(i0 * a.stride);
+        if (valid1) v1 = a.cand ? __ldg(a.cand + i1 * a.stride) : static_cast<uint32_t>(i1 * a.stride);
+        const uint4* row0 = reinterpret_cast<const uint4*>(static_cast<const char*>(a.g.vemb) + v0 * row_bytes);
+        const uint4* row1 = reinterpret_cast<const uint4*>(static_cast<const char*>(a.g.vemb) + v1 * row_bytes);
+        float x0[NV * EV], x1[NV * EV];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             const int vi = s + G * k;
-            uint4 w = make_uint4(0u, 0u, 0u, 0u);
-            if (valid && vi < dv) w = __ldg(row + vi);
-            if constexpr (BF16) {
-                x[k * EV + 0] = bf_lo(w.x);
-                x[k * EV + 1] = bf_hi(w.x);
-                x[k * EV + 2] = bf_lo(w.y);
-                x[k * EV + 3] = bf_hi(w.y);
-                x[k * EV + 4] = bf_lo(w.z);
-                x[k * EV + 5] = bf_hi(w.z);
-                x[k * EV + 6] = bf_lo(w.w);
-                x[k * EV + 7] = bf_hi(w.w);
-            } else {
-                x[k * EV + 0] = __uint_as_float(w.x);
-                x[k * EV + 1] = __uint_as_float(w.y);
-                x[k * EV + 2] = __uint_as_float(w.z);
-                x[k * EV + 3] = __uint_as_float(w.w);
-            }
+            uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
+            if (valid0 && vi < dv) w0 = __ldg(row0 + vi);
+            if (valid1 && vi < dv) w1 = __ldg(row1 + vi);
+            unpack_row<BF16>(w0, x0 + k * EV);
+            unpack_row<BF16>(w1, x1 + k * EV);
         }
         for (int qi = 0; qi < nq; ++qi) {
             const float4* q4 = reinterpret_cast<const float4*>(sq + static_cast<int64_t>(qi) * d);
-            float acc = 0.f;
+            float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
                 const int vi = s + G * k;
@@ -241,24 +273,28 @@ __global__ void __launch_bounds__(kScanThreads) k_tail_scan(ScanArgs a) {
 #pragma unroll
                     for (int e4 = 0; e4 < EV / 4; ++e4) {
                         const float4 qq = q4[vi * (EV / 4) + e4];
-                        const float* xx = x + k * EV + e4 * 4;
-                        if constexpr (TRANSE) {
-                            acc += fabsf(__fsub_rn(qq.x, xx[0]));
-                            acc += fabsf(__fsub_rn(qq.y, xx[1]));
-                            acc += fabsf(__fsub_rn(qq.z, xx[2]));
-                            acc += fabsf(__fsub_rn(qq.w, xx[3]));
-                        } else {
-                            acc += qq.x * xx[0];
-                            acc += qq.y * xx[1];
-                            acc += qq.z * xx[2];
-                            acc += qq.w * xx[3];
-                        }
+                        const float* y0 = x0 + k * EV + e4 * 4;
+                        const float* y1 = x1 + k * EV + e4 * 4;
+                        acc0 += term32<TRANSE>(qq.x, y0[0]);
+                        acc1 += term32<TRANSE>(qq.x, y1[0]);
+                        acc0 += term32<TRANSE>(qq.y, y0[1]);
+                        acc1 += term32<TRANSE>(qq.y, y1[1]);
+                        acc0 += term32<TRANSE>(qq.z, y0[2]);
+                        acc1 += term32<TRANSE>(qq.z, y1[2]);
+                        acc0 += term32<TRANSE>(qq.w, y0[3]);
+                        acc1 += term32<TRANSE>(qq.w, y1[3]);
                     }
                 }
             }
-            for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            const float s32 = TRANSE ? __fsub_rn(gamma32, acc) : acc;
-            append(a, qi, valid && s == 0 && s32 >= sthr[qi], s32, v, lane);
+            for (int o = G >> 1; o > 0; o >>= 1) {
+                acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+                acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+            }
+            const float s0 = TRANSE ? __fsub_rn(gamma32, acc0) : acc0;
+            const float s1 = TRANSE ? __fsub_rn(gamma32, acc1) : acc1;
+            const float thr = sthr[qi];
+            emit(a, qi, valid0, s == 0, s0, v0, i0, lane, thr);
+            emit(a, qi, valid1, s == 0, s1, v1, i1, lane, thr);
         }
     }
 }
@@ -271,6 +307,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tail_scan_any(ScanArgs a) {
     const int d = a.g.d, nq = a.nq;
     float* sthr = sq + static_cast<int64_t>(nq) * d;
     load_queries(a, sq, sthr);
+    keep_all_counts(a);
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * kScanWarps;
     const float gamma32 = a.g.gamma32;
@@ -287,7 +324,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tail_scan_any(ScanArgs a) {
             }
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             const float s32 = TRANSE ? __fsub_rn(gamma32, acc) : acc;
-            append(a, qi, lane == 0 && s32 >= sthr[qi], s32, v, lane);
+            emit(a, qi, true, lane == 0, s32, v, i, lane, sthr[qi]);
         }
     }
 }
@@ -423,35 +460,100 @@ __device__ __forceinline__ bool ranks_before(const BandRec& x, const BandRec& y)
     return x.w > y.w || (x.w == y.w && x.v < y.v);
 }
 
+constexpr int kQ64Max = 2048;  // rows up to this length use the shared fp64 query vector
+
+template <bool TRANSE>
+__device__ __forceinline__ double term64(double q, float c) {
+    if constexpr (TRANSE) return fabs(__dsub_rn(q, static_cast<double>(c)));
+    else return __dmul_rn(q, static_cast<double>(c));
+}
+
+// w(h, r, v) in the canonical order, with q64[j] = e_h[j] + w_r[j] (TransE)
+// or e_h[j] * w_r[j] (DistMult) already formed in fp64: the same operations
+// on the same values as the reference definition, j = 0..d-1 in order
+template <bool TRANSE>
+__device__ double rescore_row(const DevGraph& g, const double* q64, uint32_t v) {
+    const int d = g.d;
+    double acc = 0.0;
+    if (g.dtype == MHR_F32 && (d & 3) == 0) {
+        const float4* c4 = reinterpret_cast<const float4*>(static_cast<const float*>(g.vemb) + static_cast<int64_t>(v) * d);
+#pragma unroll 4
+        for (int j4 = 0; j4 < (d >> 2); ++j4) {
+            const float4 c = __ldg(c4 + j4);
+            const double* q = q64 + 4 * j4;
+            acc = __dadd_rn(acc, term64<TRANSE>(q[0], c.x));
+            acc = __dadd_rn(acc, term64<TRANSE>(q[1], c.y));
+            acc = __dadd_rn(acc, term64<TRANSE>(q[2], c.z));
+            acc = __dadd_rn(acc, term64<TRANSE>(q[3], c.w));
+        }
+    } else if (g.dtype == MHR_BF16 && (d & 7) == 0) {
+        const uint4* c8 = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(g.vemb) + static_cast<int64_t>(v) * d);
+#pragma unroll 2
+        for (int j8 = 0; j8 < (d >> 3); ++j8) {
+            const uint4 w = __ldg(c8 + j8);
+            const double* q = q64 + 8 * j8;
+            acc = __dadd_rn(acc, term64<TRANSE>(q[0], bf_lo(w.x)));
+            acc = __dadd_rn(acc, term64<TRANSE>(q[1], bf_hi(w.x)));
+            acc = __dadd_rn(acc, term64<TRANSE>(q[2], bf_lo(w.y)));
+            acc = __dadd_rn(acc, term64<TRANSE>(q[3], bf_hi(w.y)));
+            acc = __dadd_rn(acc, term64<TRANSE>(q[4], bf_lo(w.z)));
+            acc = __dadd_rn(acc, term64<TRANSE>(q[5], bf_hi(w.z)));
+            acc = __dadd_rn(acc, term64<TRANSE>(q[6], bf_lo(w.w)));
+            acc = __dadd_rn(acc, term64<TRANSE>(q[7], bf_hi(w.w)));
+        }
+    } else {
+        for (int j = 0; j < d; ++j) acc = __dadd_rn(acc, term64<TRANSE>(q64[j], emb_f32(g.vemb, g.dtype, v, d, j)));
+    }
+    return TRANSE ? __dsub_rn(g.gamma, acc) : acc;
+}
+
 __global__ void __launch_bounds__(kFinalThreads)
     k_tail_final(DevGraph g, const uint32_t* __restrict__ h, const uint16_t* __restrict__ r,
                  const SurvRec* __restrict__ surv, int64_t cap, const unsigned* __restrict__ cnt,
                  BandRec* __restrict__ band, int K, double E2, mhr_tail* __restrict__ out,
                  int32_t* __restrict__ n_out, unsigned* __restrict__ band_cnt) {
     __shared__ SelectSmem sm;
-    extern __shared__ BandRec sbuf[];  // kSortMax records
+    extern __shared__ BandRec sbuf[];  // kSortMax records, then the fp64 query vector
+    double* q64 = reinterpret_cast<double*>(sbuf + kSortMax);
     const int q = blockIdx.x;
     if (static_cast<int64_t>(cnt[q]) > cap) return;  // overflowed: rescanned alone by the host
     const int64_t n = cnt[q];
     const SurvRec* a = surv + static_cast<int64_t>(q) * cap;
     BandRec* b = band + static_cast<int64_t>(q) * cap;
+    const uint32_t hq = h[q], rq = r[q];
+    const bool transe = g.fn == MHR_SCORE_TRANSE_L1;
+    const bool shared_q = g.d <= kQ64Max;
 
     // 1. the band: survivors within 2E of the K-th best fp32 score
     double lo = -INFINITY;
     if (n > K) lo = __dsub_rd(static_cast<double>(select_kth_score(a, n, K, sm)), E2);
     if (threadIdx.x == 0) sm.count = 0u;
+    if (shared_q) {
+        for (int j = threadIdx.x; j < g.d; j += blockDim.x) {
+            const double e = static_cast<double>(emb_f32(g.vemb, g.dtype, hq, g.d, j));
+            const double w = static_cast<double>(emb_f32(g.remb, g.dtype, rq, g.d, j));
+            q64[j] = transe ? __dadd_rn(e, w) : __dmul_rn(e, w);
+        }
+    }
     __syncthreads();
-    const uint32_t hq = h[q], rq = r[q];
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         const SurvRec x = a[i];
         if (static_cast<double>(x.s) >= lo) {
-            const double w = edge_w64(g, hq, rq, x.v);
             const unsigned p = atomicAdd(&sm.count, 1u);
-            b[p] = BandRec{w, x.v, 0u};
+            b[p].v = x.v;
         }
     }
     __syncthreads();
     const unsigned nb = sm.count;
+    // fp64 rescoring, one band member per thread over dense warps
+    for (unsigned p = threadIdx.x; p < nb; p += blockDim.x) {
+        const uint32_t v = b[p].v;
+        double w;
+        if (!shared_q) w = edge_w64(g, hq, rq, v);
+        else if (transe) w = rescore_row<true>(g, q64, v);
+        else w = rescore_row<false>(g, q64, v);
+        b[p] = BandRec{w, v, 0u};
+    }
     __syncthreads();
 
     // 2. the records to sort: the whole band, or exactly its K best
@@ -534,13 +636,15 @@ cudaError_t grow(void** p, size_t* have, size_t want) {
 struct ScanKernel {
     void (*fn)(ScanArgs) = nullptr;
     int G = 1;
+    int rows_per_group = 1;
 };
 
 ScanKernel pick_scan(const DevGraph& dg) {
     const bool transe = dg.fn == MHR_SCORE_TRANSE_L1;
     const int d = dg.d;
     const bool bf = dg.dtype == MHR_BF16;
-    const int ev = bf ? 8 : 4, nvmax = bf ? 4 : 8;
+    // two rows per lane group: at most 16 elements of each row per lane
+    const int ev = bf ? 8 : 4, nvmax = bf ? 2 : 4;
     ScanKernel k;
     if (d % ev == 0 && d / ev <= 32 * nvmax) {
         const int dv = d / ev;
@@ -550,19 +654,19 @@ ScanKernel pick_scan(const DevGraph& dg) {
         int NV = 1;
         while (NV < need) NV <<= 1;
         k.G = G;
+        k.rows_per_group = 2;
         if (bf) {
             if (NV == 1) k.fn = transe ? k_tail_scan<1, true, true> : k_tail_scan<1, true, false>;
-            else if (NV == 2) k.fn = transe ? k_tail_scan<2, true, true> : k_tail_scan<2, true, false>;
-            else k.fn = transe ? k_tail_scan<4, true, true> : k_tail_scan<4, true, false>;
+            else k.fn = transe ? k_tail_scan<2, true, true> : k_tail_scan<2, true, false>;
         } else {
             if (NV == 1) k.fn = transe ? k_tail_scan<1, false, true> : k_tail_scan<1, false, false>;
             else if (NV == 2) k.fn = transe ? k_tail_scan<2, false, true> : k_tail_scan<2, false, false>;
-            else if (NV == 4) k.fn = transe ? k_tail_scan<4, false, true> : k_tail_scan<4, false, false>;
-            else k.fn = transe ? k_tail_scan<8, false, true> : k_tail_scan<8, false, false>;
+            else k.fn = transe ? k_tail_scan<4, false, true> : k_tail_scan<4, false, false>;
         }
         return k;
     }
     k.G = 32;
+    k.rows_per_group = 1;
     k.fn = transe ? k_tail_scan_any<true> : k_tail_scan_any<false>;
     return k;
 }
@@ -574,7 +678,7 @@ mhr_status launch_scan(const mhr_graph* g, const ScanKernel& sk, const ScanArgs&
     int per_sm = 0;
     MHR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk.fn, kScanThreads, smem));
     per_sm = std::max(1, per_sm);
-    const int cpw = 32 / sk.G;
+    const int cpw = sk.rows_per_group * (32 / sk.G);
     const int64_t ntiles = (a.n_visit + cpw - 1) / cpw;
     const int64_t need = (ntiles + kScanWarps - 1) / kScanWarps;
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(std::max(1, g->num_sms)) * per_sm)));
@@ -717,7 +821,7 @@ extern "C" mhr_status mhr_tail_topk(const mhr_graph* gc, int32_t nq, const uint3
 
     const double E2 = 2.0 * (g->eps32_edge + g->eps64_edge) * (1.0 + 1e-6);
     const ScanKernel sk = pick_scan(g->dg);
-    const size_t final_smem = sizeof(BandRec) * kSortMax;
+    const size_t final_smem = sizeof(BandRec) * kSortMax + (d <= kQ64Max ? sizeof(double) * d : 0);
     MHR_CUDA_TRY(cudaFuncSetAttribute(k_tail_final, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(final_smem)));
 
     int64_t n_pairs = 0, n_surv = 0, n_band = 0, n_rescan = 0;

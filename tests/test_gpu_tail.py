@@ -68,8 +68,9 @@ def test_tiny_workload(mhr, fn, cand_type, K):
                                      ("f32", 1040), ("bf16", 8), ("bf16", 40), ("bf16", 20),
                                      ("bf16", 128)])
 def test_row_formats(mhr, fn, dtype, d):
-    # 8/12/128/256 fp32 and 8/40/128 bf16: register rows (12: a padded vector
-    # count); 10 fp32, 20 bf16, 1040 fp32: the any-length kernel
+    # 8/12/128/256 fp32 and 8/40/128 bf16: register rows, two per lane group
+    # (12: a padded vector count); 10 fp32, 20 bf16 (not whole 16-byte
+    # vectors) and 1040 fp32 (above 512): the any-length kernel
     rng = np.random.default_rng(d)
     n = 12000 if d < 1000 else 3000
     g = random_kg(rng, n, 3 * n, 5, d, dtype=dtype, scale=0.3)
