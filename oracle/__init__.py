@@ -7,9 +7,10 @@ the CUDA package never imports it.
 Two independent routes compute the same result:
   * ``mhr_oracle.c`` (brute force, fp64, canonical operation order) through
     ctypes: ``edge_weights``, ``topk_paths``, ``topk_paths_batch``,
-    ``query_stats``, and the tail-prediction scan of Alg. 3 / Alg. 4,
+    ``query_stats``, the tail-prediction scan of Alg. 3 / Alg. 4,
     ``tail_topk`` (every candidate vertex of one type scored against a
-    (head, relation) pair, the K best kept);
+    (head, relation) pair, the K best kept), and the generic H-hop search with
+    a per-path beam of Alg. 6 / Alg. 7, ``beam_paths``;
   * ``mitm.py``: a pure-Python meet-in-the-middle enumeration with its own
     edge-weight loop, used to cross-check the brute force on small graphs.
 """
@@ -38,6 +39,9 @@ BF16 = 1
 PATH_DTYPE = np.dtype([("score", "<f8"), ("u", "<u4"), ("v", "<u4"),
                        ("r1", "<u2"), ("r2", "<u2"), ("r3", "<u2"), ("pad", "<u2")])
 TAIL_DTYPE = np.dtype([("score", "<f8"), ("v", "<u4"), ("pad", "<u4")])
+BEAM_MAX_H = 8
+BPATH_DTYPE = np.dtype([("score", "<f8"), ("hops", "<i4"), ("v", "<u4", (BEAM_MAX_H + 1,)),
+                        ("r", "<u2", (BEAM_MAX_H,))])
 STATS_DTYPE = np.dtype([(k, "<i8") for k in
                         ("deg_s", "deg_t", "n_u", "n_v", "s_f", "s_b", "hits", "paths")])
 
@@ -81,6 +85,9 @@ def _load():
         lib.oracle_tail_topk_batch.restype = i32
         lib.oracle_tail_topk_batch.argtypes = [P, i64, i64, P, P, i32, i32, i32, f64, i64, P, P,
                                                i32, i64, P, P, P]
+        lib.oracle_beam_paths.restype = i32
+        lib.oracle_beam_paths.argtypes = [P, P, P, i64, P, P, i32, i32, i32, f64, u32, u32, i32, i64, P, P,
+                                          P]
         lib.oracle_num_threads.restype = i32
         lib.oracle_num_threads.argtypes = []
         _lib = lib
@@ -187,6 +194,28 @@ def tail_topk(g, H, Rq, K: int, cand_type: int = -1, fn="transe", gamma=1.0):
     if rc:
         raise RuntimeError(f"oracle_tail_topk_batch: {rc}")
     return out, n_out
+
+
+def beam_paths(g, s: int, t: int, H: int, K: int, fn="transe", gamma=1.0, with_expanded=False):
+    """Generic H-hop search with a per-path beam of width K (Alg. 6 / Alg. 7):
+    the K best s->t paths of at most H hops the beam reaches, best first
+    (structured array of BPATH_DTYPE: score, hops, v[0..hops], r[0..hops-1])."""
+    assert BPATH_DTYPE.itemsize == 64
+    lib = _load()
+    G = _G(g)
+    out = np.zeros(max(int(K), 1), dtype=BPATH_DTYPE)
+    n_out = np.zeros(1, dtype=np.int64)
+    expanded = np.zeros(1, dtype=np.int64)
+    rc = lib.oracle_beam_paths(_ptr(G.offsets), _ptr(G.cols), _ptr(G.rels), G.n, _ptr(G.vemb),
+                               _ptr(G.remb), G.dtype, G.d, FN_CODES[fn], float(gamma), int(s), int(t),
+                               int(H), int(K), _ptr(out), _ptr(n_out), _ptr(expanded))
+    if rc == 1:
+        raise ValueError("invalid beam query (s, t out of range, s == t, K <= 0, H outside [1, 8], "
+                         "or K^(H-1) above 1e6)")
+    if rc:
+        raise RuntimeError(f"oracle_beam_paths: {rc}")
+    res = out[: int(n_out[0])].copy()
+    return (res, int(expanded[0])) if with_expanded else res
 
 
 def query_stats(g, s: int, t: int) -> dict:

@@ -324,6 +324,185 @@ int oracle_tail_topk_batch(const uint8_t* vtypes, int64_t n, int64_t R, const vo
     return any;
 }
 
+/* ------------------------------------------------------------------------ */
+/*
+ * Generic H-hop search with a per-path beam [Alg. 6 and Alg. 7]:
+ *   level 0 holds the one-vertex path (s).  At each of the H levels every held
+ *   path p, whose last vertex is x, is extended by every out-edge (x, r, y)
+ *   with y not already on p [Alg. 7 skips a neighbour already on the path]:
+ *     score(p + (r, y)) = score(p) + w(x, r, y)      (fp64, left to right)
+ *   - y == t: the extended path is a result [reaching the target ends the
+ *     path]; the K best results are kept (one bounded heap for the query);
+ *   - otherwise it competes in p's own bounded heap of K extensions, and the
+ *     K best of that heap are the paths p contributes to the next level
+ *     [UpdateNextPaths in Alg. 7 moves the local heap into the next array].
+ *   Paths held after the last level are dropped.  The beam is per path: level
+ *   l holds up to K^l paths (the bound Alg. 6 computes for its path arrays).
+ * Orders (total, so the result is unique):
+ *   within one path's heap: score descending, then (r, y) ascending (the
+ *     extensions of one path differ only in their last edge);
+ *   results: score descending, then hop count ascending, then the sequence
+ *     (y_1, r_1, y_2, r_2, ..., y_{h-1}, r_{h-1}, r_h) ascending, which for
+ *     three hops is (u, r1, v, r2, r3) as in the three-hop search.
+ * The generic ExtendEmbedding / ComputeScore of Alg. 7 are read as the sum of
+ * the edge weights, as in the three-hop search.
+ */
+#define ORACLE_BEAM_MAX_H 8
+
+typedef struct {
+    double score;
+    int32_t hops;
+    uint32_t v[ORACLE_BEAM_MAX_H + 1];   /* v[0] = s, v[hops] = last vertex */
+    uint16_t r[ORACLE_BEAM_MAX_H];       /* r[i]: relation of edge v[i] -> v[i+1] */
+} oracle_bpath;
+
+/* 1 if a ranks strictly before b among the results */
+static int beam_result_before(const oracle_bpath* a, const oracle_bpath* b) {
+    if (a->score != b->score) return a->score > b->score;
+    if (a->hops != b->hops) return a->hops < b->hops;
+    for (int i = 1; i < a->hops; ++i) {
+        if (a->v[i] != b->v[i]) return a->v[i] < b->v[i];
+        if (a->r[i - 1] != b->r[i - 1]) return a->r[i - 1] < b->r[i - 1];
+    }
+    return a->r[a->hops - 1] < b->r[b->hops - 1];
+}
+
+/* 1 if a ranks strictly before b among the extensions of one path */
+static int beam_ext_before(const oracle_bpath* a, const oracle_bpath* b) {
+    if (a->score != b->score) return a->score > b->score;
+    const int h = a->hops;
+    if (a->r[h - 1] != b->r[h - 1]) return a->r[h - 1] < b->r[h - 1];
+    return a->v[h] < b->v[h];
+}
+
+typedef int (*bpath_before)(const oracle_bpath*, const oracle_bpath*);
+
+/* bounded heap of the best `cap` paths; the root is the worst kept one */
+typedef struct {
+    oracle_bpath* a;
+    int64_t size, cap;
+    bpath_before before;
+} bheap;
+
+static void bheap_push(bheap* h, const oracle_bpath* p) {
+    oracle_bpath tmp;
+    if (h->size < h->cap) {
+        int64_t i = h->size++;
+        h->a[i] = *p;
+        while (i > 0) {
+            int64_t par = (i - 1) / 2;
+            if (!h->before(&h->a[par], &h->a[i])) break;
+            tmp = h->a[par];
+            h->a[par] = h->a[i];
+            h->a[i] = tmp;
+            i = par;
+        }
+        return;
+    }
+    if (!h->before(p, &h->a[0])) return;
+    h->a[0] = *p;
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, w = i;
+        if (l < h->size && h->before(&h->a[w], &h->a[l])) w = l;
+        if (r < h->size && h->before(&h->a[w], &h->a[r])) w = r;
+        if (w == i) break;
+        tmp = h->a[w];
+        h->a[w] = h->a[i];
+        h->a[i] = tmp;
+        i = w;
+    }
+}
+
+/* pop everything, best first, into out (the heap is emptied) */
+static void bheap_drain_sorted(bheap* h, oracle_bpath* out) {
+    int64_t n = h->size;
+    for (int64_t k = n - 1; k >= 0; --k) {
+        out[k] = h->a[0];                    /* the worst remaining */
+        h->a[0] = h->a[--h->size];
+        int64_t i = 0;
+        for (;;) {
+            int64_t l = 2 * i + 1, r = l + 1, w = i;
+            if (l < h->size && h->before(&h->a[w], &h->a[l])) w = l;
+            if (r < h->size && h->before(&h->a[w], &h->a[r])) w = r;
+            if (w == i) break;
+            oracle_bpath tmp = h->a[w];
+            h->a[w] = h->a[i];
+            h->a[i] = tmp;
+            i = w;
+        }
+    }
+}
+
+int oracle_beam_paths(const int64_t* offsets, const uint32_t* cols, const uint16_t* rels, int64_t n,
+                      const void* vemb, const void* remb, int dtype, int d, int fn, double gamma,
+                      uint32_t s, uint32_t t, int32_t H, int64_t K, oracle_bpath* out, int64_t* n_out,
+                      int64_t* expanded_out) {
+    if ((int64_t)s >= n || (int64_t)t >= n || s == t || K <= 0 || H < 1 || H > ORACLE_BEAM_MAX_H)
+        return ORACLE_EINVAL;
+    /* level l holds at most K^l paths; the caller keeps K^(H-1) within memory */
+    double cap_d = 1.0;
+    for (int l = 0; l < H - 1; ++l) cap_d *= (double)K;
+    if (cap_d > 1e6) return ORACLE_EINVAL;
+    const int64_t cap = (int64_t)cap_d;
+    oracle_bpath* curr = (oracle_bpath*)calloc((size_t)cap, sizeof(oracle_bpath));
+    oracle_bpath* next = (oracle_bpath*)calloc((size_t)cap, sizeof(oracle_bpath));
+    bheap res = {(oracle_bpath*)malloc(sizeof(oracle_bpath) * (size_t)K), 0, K, beam_result_before};
+    bheap loc = {(oracle_bpath*)malloc(sizeof(oracle_bpath) * (size_t)K), 0, K, beam_ext_before};
+    if (!curr || !next || !res.a || !loc.a) {
+        free(curr);
+        free(next);
+        free(res.a);
+        free(loc.a);
+        return ORACLE_ENOMEM;
+    }
+    int64_t n_curr = 1, n_next, expanded = 0;
+    curr[0].score = 0.0;
+    curr[0].hops = 0;
+    curr[0].v[0] = s;
+    for (int level = 0; level < H; ++level) {
+        n_next = 0;
+        for (int64_t p = 0; p < n_curr; ++p) {
+            const oracle_bpath* path = &curr[p];
+            const uint32_t x = path->v[path->hops];
+            loc.size = 0;
+            ++expanded;
+            for (int64_t e = offsets[x]; e < offsets[x + 1]; ++e) {
+                const uint32_t y = cols[e];
+                int on_path = 0;
+                for (int i = 0; i <= path->hops; ++i)
+                    if (path->v[i] == y) on_path = 1;
+                if (on_path) continue;
+                oracle_bpath q = *path;
+                q.score = path->score + oracle_edge_weight(vemb, remb, dtype, d, fn, gamma, x, rels[e], y);
+                q.r[q.hops] = rels[e];
+                q.hops += 1;
+                q.v[q.hops] = y;
+                if (y == t) bheap_push(&res, &q);
+                else bheap_push(&loc, &q);
+            }
+            if (level + 1 < H) {     /* p's K best extensions go to the next level */
+                const int64_t c = loc.size;
+                bheap_drain_sorted(&loc, next + n_next);
+                n_next += c;
+            }
+        }
+        oracle_bpath* tmp = curr;
+        curr = next;
+        next = tmp;
+        n_curr = n_next;
+    }
+    const int64_t nr = res.size;
+    bheap_drain_sorted(&res, out);
+    *n_out = nr;
+    if (expanded_out) *expanded_out = expanded;
+    free(curr);
+    free(next);
+    free(res.a);
+    free(loc.a);
+    return ORACLE_OK;
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();
