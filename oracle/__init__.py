@@ -7,7 +7,8 @@ the CUDA package never imports it.
 Two independent routes compute the same result:
   * ``mhr_oracle.c`` (brute force, fp64, canonical operation order) through
     ctypes: ``edge_weights``, ``topk_paths``, ``topk_paths_batch``,
-    ``query_stats``, the tail-prediction scan of Alg. 3 / Alg. 4,
+    ``query_stats``, ``topk_paths_masked`` (relation and vertex-type
+    constraints per hop, the query shape of Sec. 3.1), the tail-prediction scan of Alg. 3 / Alg. 4,
     ``tail_topk`` (every candidate vertex of one type scored against a
     (head, relation) pair, the K best kept), and the generic H-hop search with
     a per-path beam of Alg. 6 / Alg. 7, ``beam_paths``;
@@ -85,6 +86,9 @@ def _load():
         lib.oracle_tail_topk_batch.restype = i32
         lib.oracle_tail_topk_batch.argtypes = [P, i64, i64, P, P, i32, i32, i32, f64, i64, P, P,
                                                i32, i64, P, P, P]
+        lib.oracle_topk_paths_masked.restype = i32
+        lib.oracle_topk_paths_masked.argtypes = [P, P, P, i64, P, P, P, i32, i32, i32, f64, u32, u32, P, P, P,
+                                                 P, P, i64, P, P]
         lib.oracle_beam_paths.restype = i32
         lib.oracle_beam_paths.argtypes = [P, P, P, i64, P, P, i32, i32, i32, f64, u32, u32, i32, i64, P, P,
                                           P]
@@ -151,6 +155,38 @@ def topk_paths(g, s: int, t: int, K: int, fn="transe", gamma=1.0, with_counts=Fa
     if with_counts:
         return res, int(hits[0]), int(paths[0])
     return res
+
+
+def topk_paths_masked(g, s: int, t: int, K: int, rel1=None, rel2=None, rel3=None, types_u=None,
+                      types_v=None, fn="transe", gamma=1.0):
+    """The K best simple s->t three-hop paths whose relations lie in rel1 /
+    rel2 / rel3 and whose intermediate vertex types lie in types_u / types_v
+    (each an iterable of allowed ids; None allows every id)."""
+    lib = _load()
+    G = _G(g)
+
+    def flags(allowed, size):
+        f = np.zeros(size, dtype=np.uint8)
+        if allowed is None:
+            f[:] = 1
+        else:
+            f[np.asarray(list(allowed), dtype=np.int64)] = 1
+        return f
+
+    m1, m2, m3 = flags(rel1, g.R), flags(rel2, g.R), flags(rel3, g.R)
+    tu, tv = flags(types_u, 256), flags(types_v, 256)
+    vt = np.ascontiguousarray(g.vtypes, dtype=np.uint8)
+    out = np.zeros(max(int(K), 1), dtype=PATH_DTYPE)
+    n_out = np.zeros(1, dtype=np.int64)
+    rc = lib.oracle_topk_paths_masked(_ptr(G.offsets), _ptr(G.cols), _ptr(G.rels), G.n, _ptr(vt),
+                                      _ptr(G.vemb), _ptr(G.remb), G.dtype, G.d, FN_CODES[fn], float(gamma),
+                                      int(s), int(t), _ptr(m1), _ptr(m2), _ptr(m3), _ptr(tu), _ptr(tv),
+                                      int(K), _ptr(out), _ptr(n_out))
+    if rc == 1:
+        raise ValueError("invalid query (s, t out of range, s == t, or K <= 0)")
+    if rc:
+        raise RuntimeError(f"oracle_topk_paths_masked: {rc}")
+    return out[: int(n_out[0])].copy()
 
 
 def topk_paths_batch(g, S, T, K: int, fn="transe", gamma=1.0):

@@ -240,6 +240,62 @@ int oracle_topk_paths(const int64_t* offsets, const uint32_t* cols, const uint16
     return ORACLE_OK;
 }
 
+/*
+ * Constrained three-hop query [Sec. 3.1: hop 1 follows the award-winner
+ * relation, hop 2 the works-in relation, hop 3 the affiliated-with relation,
+ * and the intermediate entities are persons]: the same brute force as above,
+ * restricted to paths with rel_ok1[r1], rel_ok2[r2], rel_ok3[r3] (arrays of R
+ * flags) and type_ok_u[vtypes[u]], type_ok_v[vtypes[v]] (arrays of 256 flags).
+ */
+int oracle_topk_paths_masked(const int64_t* offsets, const uint32_t* cols, const uint16_t* rels,
+                             int64_t n, const uint8_t* vtypes, const void* vemb, const void* remb,
+                             int dtype, int d, int fn, double gamma, uint32_t s, uint32_t t,
+                             const uint8_t* rel_ok1, const uint8_t* rel_ok2, const uint8_t* rel_ok3,
+                             const uint8_t* type_ok_u, const uint8_t* type_ok_v, int64_t K,
+                             oracle_path* out, int64_t* n_out) {
+    if ((int64_t)s >= n || (int64_t)t >= n || s == t || K <= 0) return ORACLE_EINVAL;
+    khe h;
+    h.a = (oracle_path*)malloc(sizeof(oracle_path) * (size_t)K);
+    if (!h.a) return ORACLE_ENOMEM;
+    h.size = 0;
+    h.cap = K;
+    for (int64_t i = offsets[s]; i < offsets[s + 1]; ++i) {
+        uint32_t u = cols[i];
+        uint16_t r1 = rels[i];
+        if (u == s || u == t) continue;
+        if (!rel_ok1[r1] || !type_ok_u[vtypes[u]]) continue;
+        double w1 = oracle_edge_weight(vemb, remb, dtype, d, fn, gamma, s, r1, u);
+        for (int64_t j = offsets[u]; j < offsets[u + 1]; ++j) {
+            uint32_t v = cols[j];
+            uint16_t r2 = rels[j];
+            if (v == s || v == t || v == u) continue;
+            if (!rel_ok2[r2] || !type_ok_v[vtypes[v]]) continue;
+            int64_t k = lower_bound_u32(cols, offsets[v], offsets[v + 1], t);
+            if (k >= offsets[v + 1] || cols[k] != t) continue;
+            double w2 = oracle_edge_weight(vemb, remb, dtype, d, fn, gamma, u, r2, v);
+            for (; k < offsets[v + 1] && cols[k] == t; ++k) {
+                uint16_t r3 = rels[k];
+                if (!rel_ok3[r3]) continue;
+                double w3 = oracle_edge_weight(vemb, remb, dtype, d, fn, gamma, v, r3, t);
+                oracle_path p;
+                p.score = (w1 + w2) + w3;
+                p.u = u;
+                p.v = v;
+                p.r1 = r1;
+                p.r2 = r2;
+                p.r3 = r3;
+                p.pad = 0;
+                khe_push(&h, &p);
+            }
+        }
+    }
+    qsort(h.a, (size_t)h.size, sizeof(oracle_path), cmp_rank);
+    memcpy(out, h.a, sizeof(oracle_path) * (size_t)h.size);
+    *n_out = h.size;
+    free(h.a);
+    return ORACLE_OK;
+}
+
 /* Many queries, independent, in parallel over queries (OpenMP when built with it). */
 int oracle_topk_paths_batch(const int64_t* offsets, const uint32_t* cols, const uint16_t* rels,
                             int64_t n, const void* vemb, const void* remb, int dtype, int d, int fn,
