@@ -20,7 +20,8 @@
  * (j = 0..d-1 in order, no fused multiply-add).
  * The library also provides the tail-prediction scan of Alg. 3 / Alg. 4
  * (mhr_tail_topk): the K best candidate vertices of one type for
- * (head, relation) queries, exact in the same way.
+ * (head, relation) queries, exact in the same way; and the generic H-hop
+ * search with a per-path beam of Alg. 6 / Alg. 7 (mhr_beam_paths).
  *
  * Conventions for every entry point:
  *   - Status codes are returned, never raised; mhr_last_error() gives a
@@ -336,6 +337,41 @@ typedef struct {
 mhr_status mhr_tail_topk(const mhr_graph* g, int32_t nq, const uint32_t* h, const uint16_t* r,
                          int32_t cand_type, int32_t K, mhr_tail* out, int32_t* n_out, mhr_mem mem,
                          mhr_stats* stats, void* cuda_stream);
+
+/*
+ * Generic H-hop search with a per-path beam (Alg. 6 and Alg. 7), exact.  For
+ * each query (s[i], t[i]): level 0 holds the path (s); at each of H levels
+ * every held path p ending at x is extended by every out-edge (x, r, y) with y
+ * not on p, scored score(p) + w(x, r, y) (fp64, the reference operation
+ * order).  y == t makes a result (reaching the target ends a path); otherwise
+ * the extension competes in p's own list of K, and p's K best extensions
+ * (score desc, then relation, then vertex ascending) are held at the next
+ * level, so level l holds up to K^l paths (Alg. 6 sizes its path arrays so).
+ * The K best results are returned in the order score descending, hop count
+ * ascending, then (y_1, r_1, ..., y_{h-1}, r_{h-1}, r_h) ascending, the vertex
+ * and relation sequence after s (for three hops: (u, r1, v, r2, r3)).
+ *   out    nq*K records (query i at out[i*K]); n_out[i] = results written
+ *   mem    where s, t, out and n_out live
+ *   stats  optional: edges_scanned = out-edges scored; ms = wall time
+ * Synchronous.  MHR_EINVAL: NULL arrays, a vertex out of range, s == t,
+ * H outside [1, MHR_BEAM_MAX_H], K < 1; MHR_ERANGE: K > MHR_BEAM_K_MAX or
+ * K^(H-1) > 65536.  nq == 0 is a no-op.
+ */
+#define MHR_BEAM_MAX_H 8
+#define MHR_BEAM_K_MAX 64
+
+/* One beam-search result: v[0] = s, v[hops] = t, r[i] the relation of the
+ * edge v[i] -> v[i+1].  64 bytes. */
+typedef struct {
+    double score;
+    int32_t hops;
+    uint32_t v[MHR_BEAM_MAX_H + 1];
+    uint16_t r[MHR_BEAM_MAX_H];
+} mhr_beam_path;
+
+mhr_status mhr_beam_paths(const mhr_graph* g, int32_t nq, const uint32_t* s, const uint32_t* t, int32_t H,
+                          int32_t K, mhr_beam_path* out, int32_t* n_out, mhr_mem mem, mhr_stats* stats,
+                          void* cuda_stream);
 
 /* Thread-local description of the last non-OK status ("" if none). */
 const char* mhr_last_error(void);

@@ -46,6 +46,8 @@ from ._mhr import (  # noqa: F401
     paths_from_device,
     mhr_tail_topk,
     tails_from_device,
+    mhr_beam_paths,
+    BEAM_DTYPE,
 )
 
 from .learn import OrderingMLP, train_ordering_mlp  # noqa: E402,F401

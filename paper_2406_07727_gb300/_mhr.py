@@ -34,6 +34,10 @@ assert PATH_DTYPE.itemsize == 24
 TAIL_DTYPE = np.dtype([("score", "<f8"), ("v", "<u4"), ("pad", "<u4")])
 assert TAIL_DTYPE.itemsize == 16
 MHR_TAIL_K_MAX = 4096
+BEAM_MAX_H = 8
+BEAM_DTYPE = np.dtype([("score", "<f8"), ("hops", "<i4"), ("v", "<u4", (BEAM_MAX_H + 1,)),
+                       ("r", "<u2", (BEAM_MAX_H,))])
+assert BEAM_DTYPE.itemsize == 64
 
 
 class MhrError(RuntimeError):
@@ -78,7 +82,7 @@ class Stats(ctypes.Structure):
 EXPORTS = ("mhr_graph_load", "mhr_graph_free", "mhr_edge_scores", "mhr_topk_paths",
            "mhr_topk_paths_batched", "mhr_topk_paths_noalloc", "mhr_training_labels",
            "mhr_mlp_features", "mhr_mlp_forward", "mhr_mlp_backward", "mhr_mlp_adam",
-           "mhr_mlp_to_bf16", "mhr_tail_topk", "mhr_last_error", "mhr_version")
+           "mhr_mlp_to_bf16", "mhr_tail_topk", "mhr_beam_paths", "mhr_last_error", "mhr_version")
 
 _lock = threading.Lock()
 _lib = None
@@ -134,6 +138,8 @@ def load_library(build_if_missing: bool = True):
         lib.mhr_topk_paths_noalloc.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, i32, P, P, P]
         lib.mhr_tail_topk.restype = ctypes.c_int
         lib.mhr_tail_topk.argtypes = [P, i32, P, P, i32, i32, P, P, ctypes.c_int, ctypes.POINTER(Stats), P]
+        lib.mhr_beam_paths.restype = ctypes.c_int
+        lib.mhr_beam_paths.argtypes = [P, i32, P, P, i32, i32, P, P, ctypes.c_int, ctypes.POINTER(Stats), P]
         lib.mhr_last_error.restype = ctypes.c_char_p
         lib.mhr_last_error.argtypes = []
         lib.mhr_version.restype = ctypes.c_char_p
@@ -404,6 +410,22 @@ def mhr_tail_topk(g: Graph, H, Rq, K: int, cand_type: int = -1, out=None, n_out=
     if with_stats:
         return out, n_out, st.as_dict()
     return out, n_out
+
+
+def mhr_beam_paths(g: Graph, S, T, H: int, K: int, stream=None, with_stats: bool = False):
+    """Generic H-hop search with a per-path beam of width K (Alg. 6 / Alg. 7):
+    the K best s->t paths of at most H hops the beam reaches, per query.  Host
+    arrays in, host arrays out (out [nq, K] of BEAM_DTYPE, n_out [nq]);
+    synchronous."""
+    lib = load_library()
+    S, T = _host(S, np.uint32), _host(T, np.uint32)
+    nq = int(S.shape[0])
+    out = np.zeros((nq, max(int(K), 1)), dtype=BEAM_DTYPE)
+    n_out = np.zeros(nq, dtype=np.int32)
+    st = Stats()
+    _check(lib.mhr_beam_paths(g.handle, nq, _ptr(S), _ptr(T), int(H), int(K), _ptr(out), _ptr(n_out),
+                              MHR_MEM_HOST, ctypes.byref(st) if with_stats else None, _stream_ptr(stream)))
+    return (out, n_out, st.as_dict()) if with_stats else (out, n_out)
 
 
 def tails_from_device(buf, K: int) -> np.ndarray:
