@@ -58,6 +58,9 @@ WORKLOAD_DESCS = {
                   "fp32 embeddings ~N(0,1/sqrt(d)); 256 edge-biased queries per step, K=100, DistMult"),
     "learned": ("the precision workload's graph and 256 queries (d=256 fp32, DistMult) with K=50 "
                 "(or the K given), ordering MLP trained on 20,000 held-out queries"),
+    "beam": ("generic H-hop search with a per-path beam (Alg. 6 / Alg. 7) on the medium graph "
+             "(1,000,000 vertices, d=128 fp32, TransE-L1): the medium workload's 64 (s,t) queries, H=3, "
+             "beam K=10, the 10 best paths per query"),
     "tail": ("tail prediction (Alg. 3 / Alg. 4) on the medium graph (1,000,000 vertices, d=128 fp32, "
              "TransE-L1): a step scores 64 heads (the K persons of Alg. 4), each with its own relation, "
              "against every vertex of type 0 (~166,700 candidates), K=50; single-head line: one head "
@@ -237,10 +240,17 @@ def run_reference(args):
         g = synth.workload("medium")[0]
         S, T = tail_queries(g, TAIL_NQ, 0)
         metric = TAIL_METRIC
+    elif WORKLOAD == "beam":
+        import synth
+        os.environ.setdefault("MHR_SYNTH_CACHE", os.path.join(tempfile.gettempdir(), "mhr_synth_cache"))
+        g, S, T, _, _ = synth.workload("medium")
+        metric = BEAM_METRIC
     else:
         g, S, T, K, spec = load_workload(0)
-    # one query per oracle thread per step (the oracle runs queries in parallel)
-    per_step = max(1, min(len(S), oracle.num_threads()))
+    # one query per oracle thread per step (the oracle runs queries in parallel;
+    # the beam oracle runs one query at a time on one core)
+    cores = 1 if WORKLOAD == "beam" else oracle.num_threads()
+    per_step = max(1, min(len(S), cores))
     times = []
     qi = 0
     for step in range(args.warmup + args.steps):
@@ -249,6 +259,9 @@ def run_reference(args):
         t0 = time.perf_counter()
         if WORKLOAD == "tail":
             oracle.tail_topk(g, S[idx], T[idx], TAIL_K, cand_type=TAIL_TYPE)
+        elif WORKLOAD == "beam":
+            for i in idx:
+                oracle.beam_paths(g, int(S[i]), int(T[i]), BEAM_H, BEAM_K)
         else:
             oracle.topk_paths_batch(g, S[idx], T[idx], K)
         dt = time.perf_counter() - t0
@@ -261,8 +274,10 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": DATA,
             "config": {"workload": WORKLOAD_DESC, "queries_per_step": per_step,
-                       "note": f"CPU oracle: fp64 brute force, OpenMP over queries, {per_step} queries per step"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                       "note": (f"CPU oracle: fp64 beam search, one query at a time on one core, {per_step} "
+                                "queries per step" if WORKLOAD == "beam" else
+                                f"CPU oracle: fp64 brute force, OpenMP over queries, {per_step} queries per step")},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} queries per step cycling through the {len(S)} workload queries"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -392,6 +407,85 @@ def run_tail(args):
             "clocks": clk,
             "work_per_step": {k: st[k] for k in ("edges_scanned", "candidates", "rescored", "dense_queries")},
             "device_host_agree": agree,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    G.close()
+    return 0
+
+
+# ------------------------------------------------------------------ beam search
+BEAM_H, BEAM_K = 3, 10
+BEAM_METRIC = "beam-search queries/s (Alg. 6 / Alg. 7, H=3, K=10) on 1 GB300, results identical to oracle"
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 fp64 rate (no measured figure)
+
+
+def run_beam(args):
+    """Beam search: CUDA events around each call (queries as host arrays of
+    512 B, results copied back inside the call), L2 flushed before every call;
+    roofline of the fp64 edge scoring against the nominal fp64 rate."""
+    import torch
+    import synth
+    import paper_2406_07727_gb300 as mhr
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    os.environ.setdefault("MHR_SYNTH_CACHE", os.path.join(tempfile.gettempdir(), "mhr_synth_cache"))
+    g, S, T, _, _ = synth.workload("medium")
+    S, T = rank_queries(g, S, T, rank, "medium")
+    G = mhr.load_kg(g)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        mhr.mhr_beam_paths(G, S, T, BEAM_H, BEAM_K, stream=stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    st = None
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        out, n_out, st = mhr.mhr_beam_paths(G, S, T, BEAM_H, BEAM_K, stream=stream, with_stats=True)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    tot_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), ws, "cuda")
+    value = job_rate(len(S), ws, args.steps, tot_ms)
+    if rank == 0:
+        ms = tot_ms / args.steps
+        # TransE-L1 in fp64: an add, a subtract and an accumulate per element
+        flops = 3.0 * g.d * st["edges_scanned"]
+        achieved = flops / (ms / 1000.0) / 1e12
+        cpu = None
+        if ws == 1 and not args.no_cpu:
+            import oracle
+            oracle.build()
+            n, t0 = 0, time.perf_counter()
+            while n < len(S) and time.perf_counter() - t0 < 10.0:
+                oracle.beam_paths(g, int(S[n]), int(T[n]), BEAM_H, BEAM_K)
+                n += 1
+            dt = time.perf_counter() - t0
+            cpu = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"first {n} of the {len(S)} queries, one at a time, fp64, {dt:.2f} s"}
+        line = {
+            "metric": BEAM_METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": DATA,
+            "config": {"workload": WORKLOAD_DESCS["beam"], "queries_per_step": len(S), "H": BEAM_H,
+                       "K": BEAM_K, "l2": "flushed before every call (256 MiB write, outside the events)",
+                       "call": "mhr_beam_paths, synchronous; host arrays in and out"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 8 * len(S),
+                    "d2h_bytes_per_step": len(S) * BEAM_K * 64 + 4 * len(S)},
+            "gpu_launches": (BEAM_H + 2) * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "k_beam_level (all levels of a call)",
+                         "peak_source": "nominal GB300 fp64 rate (1.25 TFLOP/s), not measured",
+                         "fp64_flops_per_call": flops},
+            "clocks": clk,
+            "work_per_step": {"edges_scored": st["edges_scanned"]},
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
@@ -638,6 +732,8 @@ def main():
         return run_reference(args)
     if args.workload == "tail":
         return run_tail(args)
+    if args.workload == "beam":
+        return run_beam(args)
     return run_gpu(args)
 
 
