@@ -92,6 +92,9 @@ def _load():
         lib.oracle_beam_paths.restype = i32
         lib.oracle_beam_paths.argtypes = [P, P, P, i64, P, P, i32, i32, i32, f64, u32, u32, i32, i64, P, P,
                                           P]
+        lib.oracle_beam_paths_batch.restype = i32
+        lib.oracle_beam_paths_batch.argtypes = [P, P, P, i64, P, P, i32, i32, i32, f64, i64, P, P, i32, i64, P,
+                                                P, P]
         lib.oracle_num_threads.restype = i32
         lib.oracle_num_threads.argtypes = []
         _lib = lib
@@ -252,6 +255,25 @@ def beam_paths(g, s: int, t: int, H: int, K: int, fn="transe", gamma=1.0, with_e
         raise RuntimeError(f"oracle_beam_paths: {rc}")
     res = out[: int(n_out[0])].copy()
     return (res, int(expanded[0])) if with_expanded else res
+
+
+def beam_paths_batch(g, S, T, H: int, K: int, fn="transe", gamma=1.0):
+    """beam_paths for many queries, OpenMP over queries.  Returns
+    (paths [nq, K] of BPATH_DTYPE, n_out [nq])."""
+    lib = _load()
+    G = _G(g)
+    S = np.ascontiguousarray(S, dtype=np.uint32)
+    T = np.ascontiguousarray(T, dtype=np.uint32)
+    nq = S.shape[0]
+    out = np.zeros((nq, max(int(K), 1)), dtype=BPATH_DTYPE)
+    n_out = np.zeros(nq, dtype=np.int64)
+    status = np.zeros(nq, dtype=np.int32)
+    rc = lib.oracle_beam_paths_batch(_ptr(G.offsets), _ptr(G.cols), _ptr(G.rels), G.n, _ptr(G.vemb),
+                                     _ptr(G.remb), G.dtype, G.d, FN_CODES[fn], float(gamma), nq, _ptr(S),
+                                     _ptr(T), int(H), int(K), _ptr(out), _ptr(n_out), _ptr(status))
+    if rc:
+        raise ValueError(f"oracle beam batch failed on queries {np.flatnonzero(status).tolist()[:8]}")
+    return out, n_out
 
 
 def query_stats(g, s: int, t: int) -> dict:

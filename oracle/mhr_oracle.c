@@ -559,6 +559,25 @@ int oracle_beam_paths(const int64_t* offsets, const uint32_t* cols, const uint16
     return ORACLE_OK;
 }
 
+/* Many beam queries, in parallel over queries; out holds K paths per query. */
+int oracle_beam_paths_batch(const int64_t* offsets, const uint32_t* cols, const uint16_t* rels, int64_t n,
+                            const void* vemb, const void* remb, int dtype, int d, int fn, double gamma,
+                            int64_t nq, const uint32_t* S, const uint32_t* T, int32_t H, int64_t K,
+                            oracle_bpath* out, int64_t* n_out, int32_t* status) {
+    int any = ORACLE_OK;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < nq; ++q) {
+        int st = oracle_beam_paths(offsets, cols, rels, n, vemb, remb, dtype, d, fn, gamma, S[q], T[q], H, K,
+                                   out + q * K, &n_out[q], NULL);
+        status[q] = st;
+        if (st != ORACLE_OK) {
+#pragma omp atomic write
+            any = st;
+        }
+    }
+    return any;
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -163,6 +163,16 @@ def test_narrow_beam_invariants():
             assert res == sorted(res, key=_result_key)
 
 
+def test_batch_matches_single():
+    rng = np.random.default_rng(13)
+    g = random_kg(rng, 60, 700, 4, 8, scale=0.4)
+    S = rng.integers(0, g.n, size=9).astype(np.uint32)
+    T = ((S + 1 + rng.integers(0, g.n - 1, size=9)) % g.n).astype(np.uint32)
+    out, n_out = oracle.beam_paths_batch(g, S, T, 3, 5)
+    for q in range(len(S)):
+        assert _tuples(out[q][: n_out[q]]) == _tuples(oracle.beam_paths(g, int(S[q]), int(T[q]), 3, 5))
+
+
 def test_invalid_arguments():
     g = _kg(4, HAND_EDGES, HAND_VEMB, HAND_REMB)
     for args in ((0, 0, 3, 2), (0, 9, 3, 2), (0, 3, 0, 2), (0, 3, 9, 2), (0, 3, 3, 0)):
