@@ -20,6 +20,10 @@ Output: one JSON line on rank 0.
   cpu_baseline the CPU oracle (fp64 brute force, OpenMP over queries) on a
               bounded sample of the same queries
 
+--workload tail measures the tail-prediction scan (Alg. 3 / Alg. 4) and
+--workload beam the H-hop beam search (Alg. 6 / Alg. 7), each with its own
+JSON line; the other workloads are extra measurements of the three-hop search.
+
 --impl reference runs the CPU oracle as the reference arm on the same
 workload (bounded samples per step) and prints the same JSON line.
 """
@@ -112,6 +116,21 @@ def max_over_ranks(x: float, ws: int, device) -> float:
         import torch.distributed as dist
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def init_replicas(ws: int, local: int):
+    """One process per GPU under torchrun: the process group carries only the
+    timing reduction (replicas, no data-path collective)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+
+def close_replicas(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def job_rate(units_per_rank: int, ws: int, steps: int, max_ms: float) -> float:
@@ -303,6 +322,7 @@ def run_tail(args):
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
+    init_replicas(ws, local)
     os.environ.setdefault("MHR_SYNTH_CACHE", os.path.join(tempfile.gettempdir(), "mhr_synth_cache"))
     g = synth.workload("medium")[0]
     G = mhr.load_kg(g)
@@ -410,6 +430,7 @@ def run_tail(args):
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
     G.close()
+    close_replicas(ws)
     return 0
 
 
@@ -429,6 +450,7 @@ def run_beam(args):
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
+    init_replicas(ws, local)
     os.environ.setdefault("MHR_SYNTH_CACHE", os.path.join(tempfile.gettempdir(), "mhr_synth_cache"))
     g, S, T, _, _ = synth.workload("medium")
     S, T = rank_queries(g, S, T, rank, "medium")
@@ -493,6 +515,7 @@ def run_beam(args):
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
     G.close()
+    close_replicas(ws)
     return 0
 
 
