@@ -31,6 +31,10 @@
  * Tail prediction (Alg. 3, Alg. 4): oracle_tail_topk below scores every
  * candidate vertex of one type against one (head, relation) pair with the same
  * edge weight and keeps the K best (score descending, then vertex ascending).
+ * Constrained three-hop queries (Sec. 3.1): oracle_topk_paths_masked, the
+ * brute force restricted to allowed relations per hop and vertex types.
+ * Generic H-hop search with a per-path beam (Alg. 6, Alg. 7):
+ * oracle_beam_paths.
  *
  * Parity pins (tests/): hand-derived examples with dyadic embeddings, closed
  * forms (zero embeddings), the exact rational edge weight within the fp64
