@@ -208,3 +208,32 @@ def test_batch_matches_single():
         single = oracle.topk_paths(g, int(S[q]), int(T[q]), 7)
         assert n_out[q] == len(single)
         assert path_tuples(out[q, : n_out[q]]) == path_tuples(single)
+
+
+def test_top_k_merges_associatively():
+    """Alg. 2 merges thread-private K-heaps with a tree; under the total order
+    (score desc, then ids) the K best of a union are the K best of the union of
+    each part's K best, however the paths are split and in whatever order the
+    parts are merged."""
+    rng = np.random.default_rng(41)
+    g = random_kg(rng, 30, 600, 3, 4, dyadic=True)   # dyadic: many exact score ties
+    full = None
+    for _ in range(20):
+        s, t = [int(x) for x in rng.choice(g.n, size=2, replace=False)]
+        full = path_tuples(oracle.topk_paths(g, s, t, 10 ** 6))
+        if len(full) > 40:
+            break
+    assert full and len(full) > 40
+    key = lambda p: (-p[0],) + tuple(p[1:])
+    for K in (1, 7, 25):
+        want = sorted(full, key=key)[:K]
+        assert path_tuples(oracle.topk_paths(g, s, t, K)) == want   # the oracle's bounded heap
+        for workers in (2, 3, 8):
+            perm = rng.permutation(len(full))
+            parts = [[full[i] for i in perm[w::workers]] for w in range(workers)]
+            heaps = [sorted(p, key=key)[:K] for p in parts]
+            while len(heaps) > 1:                       # pairwise tree reduction
+                order = rng.permutation(len(heaps))
+                heaps = [sorted(heaps[order[i]] + (heaps[order[i + 1]] if i + 1 < len(heaps) else []),
+                                key=key)[:K] for i in range(0, len(heaps), 2)]
+            assert heaps[0] == want
