@@ -121,6 +121,29 @@ typedef struct {
     const float* b2;
 } mhr_mlp;
 
+/*
+ * Constraints of a three-hop query (Sec. 3.1): the paper's query follows
+ * award-winner, then works-in, then affiliated-with, and both intermediate
+ * entities are persons; Alg. 1 extracts those vertex sets by type.  Here each
+ * hop has a set of allowed relations and each intermediate vertex a set of
+ * allowed vertex types; a path s -r1-> u -r2-> v -r3-> t is a result only when
+ * r1, r2, r3 and the types of u and v are all allowed.  Scores, simple-path
+ * rules and the result order are those of the unconstrained search.
+ *   rel1, rel2, rel3  host arrays of n_relations bytes, nonzero = allowed;
+ *                     NULL = every relation
+ *   types_u, types_v  host arrays of 256 bytes indexed by vertex type,
+ *                     nonzero = allowed; NULL = every type
+ * The arrays are read during the call only.  They apply to every query of a
+ * batched call.
+ */
+typedef struct {
+    const uint8_t* rel1;
+    const uint8_t* rel2;
+    const uint8_t* rel3;
+    const uint8_t* types_u;
+    const uint8_t* types_v;
+} mhr_constraints;
+
 /* Query options; a NULL pointer means all defaults (zeros). */
 typedef struct {
     int32_t chunk;       /* edges per work item of the middle join: 0 = default (16384), else a
@@ -137,6 +160,10 @@ typedef struct {
     int32_t tile;        /* 32-edge groups each warp of the middle join scans per step:
                             0 = default (4), else 4 or 8 (MHR_EINVAL otherwise) */
     int32_t reserved;
+    const mhr_constraints* constraints;  /* NULL = unconstrained; see mhr_constraints.  The
+                            work counters then count the combinations of allowed hop-1 and
+                            hop-3 vertices and allowed middle edges, before the hop-1 and
+                            hop-3 relation filter.  Not with mhr_training_labels. */
 } mhr_query_opts;
 
 /* Work counters of the last call (optional output). */
@@ -163,6 +190,31 @@ mhr_status mhr_graph_load(const mhr_graph_desc* desc, mhr_graph** out, void* cud
 
 /* Release the device copy.  NULL is accepted. */
 mhr_status mhr_graph_free(mhr_graph* g);
+
+/*
+ * Sizes of a loaded graph and the proven error bounds its searches screen
+ * with.  The paper computes in fp32 (Sec. 4.2 builds with -Ofast) and states
+ * no error; these bounds are what keeps the results here exact: an fp32 edge
+ * weight is within eps32_edge of the exact one, and the fp32 score of a
+ * three-hop path within err_path of its fp64 score (err_path_tc when the
+ * middle edge comes from the bf16 tensor-core screen; DistMult only, else 0).
+ * All fields are written; out is a host pointer.  MHR_EINVAL on NULL.
+ */
+typedef struct {
+    int64_t n_vertices;
+    int64_t n_edges;
+    int32_t n_relations;
+    int32_t dim;
+    int64_t max_out_degree;
+    int64_t max_in_degree;
+    double eps32_edge;
+    double eps64_edge;
+    double err_path;
+    double epstc_edge;
+    double err_path_tc;
+} mhr_graph_info;
+
+mhr_status mhr_graph_get_info(const mhr_graph* g, mhr_graph_info* out);
 
 /*
  * Edge weights w(src[i], rel[i], dst[i]) for i < n (Alg. 3, Alg. 4 score form).

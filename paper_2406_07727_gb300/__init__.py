@@ -29,6 +29,7 @@ from ._mhr import (  # noqa: F401
     load_library,
     mhr_edge_scores,
     mhr_graph_free,
+    mhr_graph_get_info,
     mhr_graph_load,
     mhr_last_error,
     mhr_topk_paths,

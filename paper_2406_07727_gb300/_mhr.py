@@ -62,10 +62,16 @@ class MLP(ctypes.Structure):
                 ("b2", ctypes.c_void_p)]
 
 
+class Constraints(ctypes.Structure):
+    _fields_ = [("rel1", ctypes.c_void_p), ("rel2", ctypes.c_void_p), ("rel3", ctypes.c_void_p),
+                ("types_u", ctypes.c_void_p), ("types_v", ctypes.c_void_p)]
+
+
 class QueryOpts(ctypes.Structure):
     _fields_ = [("chunk", ctypes.c_int32), ("order", ctypes.c_int32), ("prune", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("mlp", ctypes.POINTER(MLP)),
-                ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("constraints", ctypes.POINTER(Constraints))]
 
 
 class Stats(ctypes.Structure):
@@ -79,7 +85,19 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ("mhr_graph_load", "mhr_graph_free", "mhr_edge_scores", "mhr_topk_paths",
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("n_edges", ctypes.c_int64),
+                ("n_relations", ctypes.c_int32), ("dim", ctypes.c_int32),
+                ("max_out_degree", ctypes.c_int64), ("max_in_degree", ctypes.c_int64),
+                ("eps32_edge", ctypes.c_double), ("eps64_edge", ctypes.c_double),
+                ("err_path", ctypes.c_double), ("epstc_edge", ctypes.c_double),
+                ("err_path_tc", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ("mhr_graph_load", "mhr_graph_free", "mhr_graph_get_info", "mhr_edge_scores", "mhr_topk_paths",
            "mhr_topk_paths_batched", "mhr_topk_paths_noalloc", "mhr_training_labels",
            "mhr_mlp_features", "mhr_mlp_forward", "mhr_mlp_backward", "mhr_mlp_adam",
            "mhr_mlp_to_bf16", "mhr_tail_topk", "mhr_beam_paths", "mhr_last_error", "mhr_version")
@@ -110,6 +128,8 @@ def load_library(build_if_missing: bool = True):
         lib.mhr_graph_load.argtypes = [ctypes.POINTER(GraphDesc), ctypes.POINTER(P), P]
         lib.mhr_graph_free.restype = ctypes.c_int
         lib.mhr_graph_free.argtypes = [P]
+        lib.mhr_graph_get_info.restype = ctypes.c_int
+        lib.mhr_graph_get_info.argtypes = [P, ctypes.POINTER(GraphInfo)]
         lib.mhr_edge_scores.restype = ctypes.c_int
         lib.mhr_edge_scores.argtypes = [P, P, P, P, i64, i32, P, ctypes.c_int, P]
         lib.mhr_topk_paths.restype = ctypes.c_int
@@ -197,7 +217,7 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _opts(opts) -> Optional[QueryOpts]:
+def _opts(opts, n_relations: int = 0) -> Optional[QueryOpts]:
     if opts is None:
         return None
     if isinstance(opts, QueryOpts):
@@ -207,9 +227,50 @@ def _opts(opts) -> Optional[QueryOpts]:
         if k == "mlp":
             o._mlp_keep = v if isinstance(v, MLP) else v.struct()
             o.mlp = ctypes.pointer(o._mlp_keep)
+        elif k == "constraints":
+            if v is not None:
+                o._cons_keep = _constraints(v, n_relations)
+                o.constraints = ctypes.pointer(o._cons_keep)
         else:
             setattr(o, k, int(v))
     return o
+
+
+def _constraints(c, n_relations: int) -> Constraints:
+    """{"rel1", "rel2", "rel3": allowed relation ids per hop, "types_u",
+    "types_v": allowed vertex types of u and v} -> mhr_constraints; a missing
+    or None entry allows every id.  Relation flags have the graph's
+    n_relations entries (the library reads that many)."""
+    if isinstance(c, Constraints):
+        return c
+    c = dict(c)
+    n_rel = int(n_relations)
+    out = Constraints()
+    keep = []
+    for name in ("rel1", "rel2", "rel3"):
+        ids = c.get(name)
+        if ids is None:
+            continue
+        ids = np.asarray(list(ids), dtype=np.int64)
+        if ids.size and (ids.min() < 0 or ids.max() >= n_rel):
+            raise ValueError(f"{name}: relation id outside [0, {n_rel})")
+        f = np.zeros(max(n_rel, 1), dtype=np.uint8)
+        f[ids] = 1
+        keep.append(f)
+        setattr(out, name, f.ctypes.data)
+    for name in ("types_u", "types_v"):
+        ids = c.get(name)
+        if ids is None:
+            continue
+        ids = np.asarray(list(ids), dtype=np.int64)
+        if ids.size and (ids.min() < 0 or ids.max() > 255):
+            raise ValueError(f"{name}: vertex type outside [0, 255]")
+        f = np.zeros(256, dtype=np.uint8)
+        f[ids] = 1
+        keep.append(f)
+        setattr(out, name, f.ctypes.data)
+    out._keep = keep
+    return out
 
 
 # --------------------------------------------------------------------------- API
@@ -276,6 +337,13 @@ def mhr_graph_free(g: Graph):
     g.close()
 
 
+def mhr_graph_get_info(g: Graph) -> dict:
+    """Sizes and proven fp32 screening error bounds of a loaded graph."""
+    info = GraphInfo()
+    _check(load_library().mhr_graph_get_info(g.handle, ctypes.byref(info)))
+    return info.as_dict()
+
+
 def mhr_edge_scores(g: Graph, src=None, rel=None, dst=None, precision: int = 0, out=None,
                     stream=None):
     """Edge weights; precision 0 -> float32 (fp32 arithmetic), 2 -> float64
@@ -303,7 +371,7 @@ def mhr_topk_paths(g: Graph, s: int, t: int, K: int, opts=None, with_stats: bool
     out = np.zeros(max(int(K), 1), dtype=PATH_DTYPE)
     n_out = ctypes.c_int32(0)
     st = Stats()
-    o = _opts(opts)
+    o = _opts(opts, g.R)
     rc = lib.mhr_topk_paths(g.handle, ctypes.c_uint32(int(s) & 0xFFFFFFFF),
                             ctypes.c_uint32(int(t) & 0xFFFFFFFF), int(K), _ptr(out),
                             ctypes.byref(n_out), ctypes.byref(o) if o is not None else None,
@@ -334,7 +402,7 @@ def mhr_topk_paths_batched(g: Graph, S, T, K: int, out=None, n_out=None, opts=No
         if n_out is None:
             n_out = torch.empty(nq, dtype=torch.int32, device=S.device)
     st = Stats()
-    o = _opts(opts)
+    o = _opts(opts, g.R)
     rc = lib.mhr_topk_paths_batched(g.handle, nq, _ptr(S), _ptr(T), int(K), _ptr(out), _ptr(n_out),
                                     mem, ctypes.byref(o) if o is not None else None,
                                     ctypes.byref(st) if with_stats else None, _stream_ptr(stream))
@@ -357,7 +425,7 @@ def mhr_autotune(g: Graph, S, T, K: int, opts=None, chunks=(4096, 8192, 16384), 
     tl = np.ascontiguousarray(tiles, dtype=np.int32)
     ms = np.zeros(2 * len(ch) * len(tl), dtype=np.float32)
     bc, bt, bp = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
-    o = _opts(opts)
+    o = _opts(opts, g.R)
     _check(lib.mhr_autotune(g.handle, int(S.shape[0]), _ptr(S), _ptr(T), int(K), mem,
                             ctypes.byref(o) if o is not None else None, _ptr(ch), len(ch), _ptr(tl), len(tl),
                             int(reps), ctypes.byref(bc), ctypes.byref(bt), ctypes.byref(bp), _ptr(ms),

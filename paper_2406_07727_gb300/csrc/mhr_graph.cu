@@ -18,7 +18,9 @@
 
 static_assert(sizeof(mhr_graph_desc) == 104, "mhr_graph_desc layout");
 static_assert(sizeof(mhr_path) == 24, "mhr_path layout");
-static_assert(sizeof(mhr_query_opts) == 32, "mhr_query_opts layout");
+static_assert(sizeof(mhr_query_opts) == 40, "mhr_query_opts layout");
+static_assert(sizeof(mhr_constraints) == 40, "mhr_constraints layout");
+static_assert(sizeof(mhr_graph_info) == 80, "mhr_graph_info layout");
 static_assert(sizeof(mhr_mlp) == 32, "mhr_mlp layout");
 static_assert(sizeof(mhr_stats) == 80, "mhr_stats layout");
 
@@ -659,6 +661,23 @@ extern "C" mhr_status mhr_edge_scores(const mhr_graph* g, const uint32_t* src, c
         MHR_CUDA_TRY(cudaMemcpyAsync(out, dout, osz * n, cudaMemcpyDeviceToHost, st));
         MHR_CUDA_TRY(cudaStreamSynchronize(st));
     }
+    return MHR_OK;
+}
+
+extern "C" mhr_status mhr_graph_get_info(const mhr_graph* g, mhr_graph_info* out) {
+    MHR_TRY(check_graph(g));
+    if (!out) return fail(MHR_EINVAL, "out is NULL");
+    out->n_vertices = g->dg.n;
+    out->n_edges = g->dg.E;
+    out->n_relations = g->dg.R;
+    out->dim = g->dg.d;
+    out->max_out_degree = g->max_out_deg;
+    out->max_in_degree = g->max_in_deg;
+    out->eps32_edge = g->eps32_edge;
+    out->eps64_edge = g->eps64_edge;
+    out->err_path = g->err_path;
+    out->epstc_edge = g->epstc_edge;
+    out->err_path_tc = g->err_path_tc;
     return MHR_OK;
 }
 

@@ -255,8 +255,30 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, D
             const bool excl = (vtx == s) || (vtx == t);
             // A vertex with no scan edges can neither be scanned nor be hit, so it
             // never lies on a path: it is dropped from the distinct list.
-            const bool head = !excl && sdeg > 0 && (k == 0 || prev != vtx);
-            P->w32[x] = excl ? neg_inf() : wmine;
+            bool head = !excl && sdeg > 0 && (k == 0 || prev != vtx);
+            bool allowed = true;
+            const uint8_t* cons = P->cons;
+            if (cons) {
+                // constrained query: a slot of a disallowed hop-1 / hop-3 relation
+                // weighs -inf; a vertex heads its run only when its type is allowed
+                // and at least one edge of the run has an allowed relation
+                const int R = g.R;
+                const uint8_t* rf = cons + (sideA ? 0 : 2 * R);
+                allowed = rf[r] != 0;
+                if (head) {
+                    head = cons[3 * R + (sideA ? 0 : 256) + g.vtypes[vtx]] != 0;
+                    if (head && !allowed) {
+                        const int64_t p0 = sideA ? g.off[s] : g.roff[t];
+                        const int64_t rlen = (sideA ? g.off[s + 1] : g.roff[t + 1]) - p0;
+                        const uint32_t* cc = sideA ? g.col : g.rcol;
+                        const uint16_t* rr = sideA ? g.rel : g.rrel;
+                        bool any = false;
+                        for (int64_t j = k + 1; j < rlen && cc[p0 + j] == vtx && !any; ++j) any = rf[rr[p0 + j]] != 0;
+                        head = any;
+                    }
+                }
+            }
+            P->w32[x] = (excl || !allowed) ? neg_inf() : wmine;
             P->flag[x] = head ? 1u : 0u;
             P->w64own[x] = 0;
             key = 2u * static_cast<uint32_t>(q) + (sideA ? 0u : 1u);
@@ -1517,9 +1539,14 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                             hcl = ec.run_len;
                             mw1 = ea.maxw;
                             mw3 = ec.maxw;
-                            n_paths_w += hal * hcl;
                             alive = true;
-                            if (prune) {
+                            if (P->cons && !P->cons[g.R + hr2]) {
+                                // constrained query: a disallowed middle relation ends the hit
+                                alive = false;
+                                hal = 0;
+                            }
+                            n_paths_w += hal * hcl;
+                            if (prune && alive) {
                                 // w2 <= the largest weight of any out-edge of u and of any in-edge of v
                                 const float mw2 = fminf(ea.midw, ec.midw);
                                 if (__fadd_ru(__fadd_rn(__fadd_rn(mw1, mw2), mw3), slack) < thr) {
@@ -1570,11 +1597,13 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                             if (lane / H == r) w2m = tw;
                         }
                         hw2 = w2m;
+                        // a hit with no combination (disallowed middle relation) stays out
+                        if (hal == 0u) hw2 = neg_inf();
                         MHR_SUB(3);
                         const float smax = __fadd_rn(__fadd_rn(mw1, hw2), mw3);
                         // training labels (plain runs only): best path score through the near entry
                         if (P->label && live2) atomicMax(&P->ubest[sm.near_base + hnk], f2key(smax));
-                        pend = __ballot_sync(FULL, live2 && smax >= thr);
+                        pend = __ballot_sync(FULL, live2 && hal != 0u && smax >= thr);
                         loaded = true;
                         slice = 0;
                     }
@@ -1622,7 +1651,8 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                                     j = sl - i * o_hcl;
                                 }
                                 const float s32 = __fadd_rn(__fadd_rn(w1s[o_has + i], o_w2), w3s[o_hcs + j]);
-                                keep = s32 >= thr;
+                                // -inf: a slot of a disallowed relation (constrained queries)
+                                keep = s32 >= thr && s32 != neg_inf();
                                 cd.s32 = s32;
                                 cd.a_idx = o_has + i;
                                 cd.c_idx = o_hcs + j;
@@ -2035,7 +2065,9 @@ __global__ void __launch_bounds__(1024) k_exact(const PlanDev* __restrict__ P, D
                     sm.hnk[slot] = lo;
                     sm.hfk[slot] = a;
                     sm.hep[slot] = ep;
-                    sm.hw2[slot] = edge_w32_group(g, ea.vertex, relsrc[ep], ec.vertex, 0, 1);
+                    const uint32_t r2 = relsrc[ep];
+                    sm.hw2[slot] = (P->cons && !P->cons[g.R + r2]) ? neg_inf()
+                                                                   : edge_w32_group(g, ea.vertex, r2, ec.vertex, 0, 1);
                 }
             }
             __syncthreads();
@@ -2072,7 +2104,7 @@ __global__ void __launch_bounds__(1024) k_exact(const PlanDev* __restrict__ P, D
                     const float w3 = P->w32[c_base + ec.run_start + j];
                     const float s32 = __fadd_rn(__fadd_rn(w1, sm.hw2[lo]), w3);
                     const double thr = sm.thr64;
-                    if (static_cast<double>(s32) + err >= thr) {
+                    if (s32 != neg_inf() && static_cast<double>(s32) + err >= thr) {
                         const int64_t p1 = g.off[s] + ea.run_start + i;
                         const int64_t p3 = g.roff[t] + ec.run_start + j;
                         mhr_path p;
@@ -2186,10 +2218,13 @@ void destroy_plans(mhr_graph* g) {
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct RegionLayout {
-    size_t off_S, off_T, off_a, off_c, total;
+    size_t off_S, off_T, off_a, off_c, off_cons, total;
 };
 
-static RegionLayout region_layout(int nq) {
+// bytes of the constraint flags: three relation sets and two type sets
+static size_t cons_bytes(int R) { return 3 * static_cast<size_t>(R) + 512; }
+
+static RegionLayout region_layout(int nq, int R) {
     RegionLayout L;
     size_t o = align_up(sizeof(PlanDev), 256);
     L.off_S = o;
@@ -2200,6 +2235,8 @@ static RegionLayout region_layout(int nq) {
     o = align_up(o + sizeof(int64_t) * (nq + 1), 256);
     L.off_c = o;
     o = align_up(o + sizeof(int64_t) * (nq + 1), 256);
+    L.off_cons = o;
+    o = align_up(o + cons_bytes(R), 256);
     L.total = o;
     return L;
 }
@@ -2484,7 +2521,7 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precisio
     if ((rc = plan_alloc(p, &h.cursors, p->grid)) != MHR_OK) return bail(rc);
     if ((rc = plan_alloc(p, &h.drained, (p->grid + 31) / 32)) != MHR_OK) return bail(rc);
     h.grid = p->grid;
-    const RegionLayout L = region_layout(nq);
+    const RegionLayout L = region_layout(nq, G->dg.R);
     p->region_bytes = L.total;
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p->dregion), L.total);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc (plan region)"));
@@ -2567,7 +2604,7 @@ static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint
     Plan* p = nullptr;
     MHR_TRY(get_plan(G, nq, K, chunk, precision, tile, &p));
     // sizes from the host copy of the row starts
-    const RegionLayout L = region_layout(nq);
+    const RegionLayout L = region_layout(nq, G->dg.R);
     if (p->h2d_pending) {
         MHR_CUDA_TRY(cudaEventSynchronize(p->h2d_done));
         p->h2d_pending = false;
@@ -2621,6 +2658,21 @@ static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint
     }
     p->h.label = label ? 1 : 0;
     if (label && (p->h.prune || p->h.order)) return fail(MHR_EINVAL, "label runs use the plain search");
+    // constraint flags (Sec. 3.1 query shape), copied with the call's queries
+    p->h.cons = nullptr;
+    if (opts && opts->constraints) {
+        if (label) return fail(MHR_EINVAL, "label runs use the unconstrained search");
+        const mhr_constraints* c = opts->constraints;
+        const int R = G->dg.R;
+        uint8_t* f = p->pin + L.off_cons;
+        const uint8_t* rel[3] = {c->rel1, c->rel2, c->rel3};
+        for (int h = 0; h < 3; ++h)
+            for (int r = 0; r < R; ++r) f[h * R + r] = rel[h] ? (rel[h][r] != 0) : 1;
+        const uint8_t* ty[2] = {c->types_u, c->types_v};
+        for (int h = 0; h < 2; ++h)
+            for (int y = 0; y < 256; ++y) f[3 * R + h * 256 + y] = ty[h] ? (ty[h][y] != 0) : 1;
+        p->h.cons = p->dregion + L.off_cons;
+    }
     std::memcpy(p->pin, &p->h, sizeof(PlanDev));
     MHR_CUDA_TRY(cudaMemcpyAsync(p->dregion, p->pin, L.total, cudaMemcpyHostToDevice, st));
     MHR_CUDA_TRY(cudaEventRecord(p->h2d_done, st));

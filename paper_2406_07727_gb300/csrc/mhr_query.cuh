@@ -79,6 +79,9 @@ struct PlanDev {
     int32_t precision;     // 0 fp32 CUDA-core middle-edge screen, 1 bf16 tensor-core screen (DistMult)
     float prune_slack;     // added to every pruning bound when the middle edge comes from the tensor cores
     const uint16_t* wsplit;  // [2][R][d] bf16 hi / lo relation table
+    // constrained query: flags [rel1: R][rel2: R][rel3: R][types of u: 256][types of v: 256]
+    // (nonzero = allowed), or NULL when the call has no constraint
+    const uint8_t* cons;
     MlpDev mlp;            // order 2 weights
     int64_t nhist;        // nq * 256 order buckets
     int64_t item_cap;     // capacity of item_ub
