@@ -341,7 +341,13 @@ mhr_status mhr_mlp_to_bf16(const float* src, uint16_t* dst, int64_t count, void*
  *   before any stream capture.  Every call on a device shares the array and
  *   it keeps the last call's contents (each call writes every cell it reads),
  *   so calls that overlap on the GPU (other streams, other threads) race:
- *   serialise them.
+ *   serialise them.  The looked-up address is kept for the life of the
+ *   process; cudaDeviceReset invalidates it, so do not reset a device that
+ *   this entry point has run on and then call it again.
+ *   Cost: one thread block on one SM walks every middle edge out of the
+ *   hop-1 vertices (the sum of their out-degrees), so the time grows with
+ *   that sum; a hub source on a power-law graph can make one call take
+ *   seconds.  mhr_topk_paths_batched spreads the same work over every SM.
  */
 mhr_status mhr_topk_paths_noalloc(const mhr_graph* g, uint32_t s, uint32_t t, int32_t K, mhr_path* out,
                                   int32_t* n_out, void* cuda_stream);

@@ -903,6 +903,60 @@ __device__ __forceinline__ float hit_w32_f32(const DevGraph& g, NearRow& nr, uin
     return transe ? __fsub_rn(g.gamma32, acc) : acc;
 }
 
+// The same for bf16 rows with d = 8*vec, vec <= kHitVecs*G: 16-byte vectors of
+// eight bf16 values, widened exactly to fp32 before the fp32 arithmetic (so
+// the screening error bound is unchanged).  The near row's raw bits stay in
+// the float4 registers of nr; relc holds the bf16 relation table when it fits.
+__device__ __forceinline__ uint4 f4_bits(const float4& f) {
+    return make_uint4(__float_as_uint(f.x), __float_as_uint(f.y), __float_as_uint(f.z), __float_as_uint(f.w));
+}
+__device__ __forceinline__ float4 bits_f4(const uint4& u) {
+    return make_float4(__uint_as_float(u.x), __uint_as_float(u.y), __uint_as_float(u.z), __uint_as_float(u.w));
+}
+__device__ __forceinline__ float term8(const uint4& h, const uint4& r, const uint4& t, bool transe) {
+    const uint32_t a[4] = {h.x, h.y, h.z, h.w}, b[4] = {r.x, r.y, r.z, r.w}, c[4] = {t.x, t.y, t.z, t.w};
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        acc += term_tr(bf_lo(a[i]), bf_lo(b[i]), bf_lo(c[i]), transe);
+        acc += term_tr(bf_hi(a[i]), bf_hi(b[i]), bf_hi(c[i]), transe);
+    }
+    return acc;
+}
+
+__device__ __forceinline__ float hit_w32_bf16(const DevGraph& g, NearRow& nr, uint32_t near_v, uint32_t far_v,
+                                              uint32_t r, bool fwd, int sub, int G, int vec, const float4* relc) {
+    const uint4* E = static_cast<const uint4*>(g.vemb);
+    const uint4* Rw = static_cast<const uint4*>(g.remb);
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    bool has[kHitVecs];
+#pragma unroll
+    for (int k = 0; k < kHitVecs; ++k) has[k] = sub + k * G < vec;
+    if (near_v != nr.id) {
+#pragma unroll
+        for (int k = 0; k < kHitVecs; ++k)
+            nr.v[k] = bits_f4(has[k] ? __ldg(E + static_cast<int64_t>(near_v) * vec + sub + k * G) : z);
+        nr.id = near_v;
+    }
+    uint4 f[kHitVecs], rv[kHitVecs];
+#pragma unroll
+    for (int k = 0; k < kHitVecs; ++k) f[k] = has[k] ? __ldg(E + static_cast<int64_t>(far_v) * vec + sub + k * G) : z;
+#pragma unroll
+    for (int k = 0; k < kHitVecs; ++k) {
+        if (relc) rv[k] = has[k] ? f4_bits(relc[r * vec + sub + k * G]) : z;
+        else rv[k] = has[k] ? __ldg(Rw + static_cast<int64_t>(r) * vec + sub + k * G) : z;
+    }
+    const bool transe = g.fn == MHR_SCORE_TRANSE_L1;
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < kHitVecs; ++k) {
+        const uint4 nv = f4_bits(nr.v[k]);
+        acc += has[k] ? (fwd ? term8(nv, rv[k], f[k], transe) : term8(f[k], rv[k], nv, transe)) : 0.f;
+    }
+    for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+    return transe ? __fsub_rn(g.gamma32, acc) : acc;
+}
+
 // A query is seeded (its first kSeedEdges edges done by the seed launch) when
 // pruning is on and it has at least kSeedMinItems work items.
 __device__ __forceinline__ bool seeded_query(const PlanDev* __restrict__ P, int q, bool prune) {
@@ -1175,9 +1229,13 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
     // fast hit scorer: fp32 rows of at most 2G vectors per lane group
     const int vec4 = g.d / 4;
     const bool fast = g.dtype == MHR_F32 && (g.d & 3) == 0 && vec4 <= kHitVecs * P->hit_width;
-    const bool relc_ok = fast && g.R * vec4 <= kRelCacheVecs;
+    // the same for bf16 rows (16-byte vectors of eight values)
+    const int vec8 = g.d / 8;
+    const bool fastb = g.dtype == MHR_BF16 && (g.d & 7) == 0 && vec8 <= kHitVecs * P->hit_width;
+    const int relvecs = fast ? g.R * vec4 : (fastb ? g.R * vec8 : kRelCacheVecs + 1);
+    const bool relc_ok = relvecs <= kRelCacheVecs;
     if (relc_ok)
-        for (int i = threadIdx.x; i < g.R * vec4; i += blockDim.x)
+        for (int i = threadIdx.x; i < relvecs; i += blockDim.x)
             sm.relc[i] = reinterpret_cast<const float4*>(g.remb)[i];
     // (the first __syncthreads of the item loop publishes the cache)
 
@@ -1590,6 +1648,10 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                                 const bool fwd = sm.dir != 0;
                                 w = hit_w32_f32(g, nrow, fwd ? u : v, fwd ? v : u, rr, fwd, sub, G, vec4,
                                                 relc_ok ? sm.relc : nullptr);
+                            } else if (fastb) {
+                                const bool fwd = sm.dir != 0;
+                                w = hit_w32_bf16(g, nrow, fwd ? u : v, fwd ? v : u, rr, fwd, sub, G, vec8,
+                                                 relc_ok ? sm.relc : nullptr);
                             } else {
                                 w = edge_w32_group(g, u, rr, v, sub, G);
                             }

@@ -41,8 +41,8 @@ def masked_oracle(g, S, T, K, c, fn):
         if s == t:
             out.append(None)
             continue
-        out.append(oracle.topk_paths_masked(g, s, t, K, rel1=c["rel1"], rel2=c["rel2"], rel3=c["rel3"],
-                                            types_u=c["types_u"], types_v=c["types_v"], fn=fn))
+        out.append(oracle.topk_paths_masked(g, s, t, K, rel1=c.get("rel1"), rel2=c.get("rel2"), rel3=c.get("rel3"),
+                                            types_u=c.get("types_u"), types_v=c.get("types_v"), fn=fn))
     return out
 
 
