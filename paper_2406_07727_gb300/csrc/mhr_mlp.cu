@@ -6,28 +6,54 @@
 
 #include "mhr_internal.cuh"
 #include "mhr_mlp.cuh"
+#include "mhr_mlp_tc.cuh"
 
 namespace mhr {
 
 constexpr int kMlpParams = kMlpHid * kMlpIn + kMlpHid + kMlpHid + 1;  // W1, b1, w2, b2
 
-__global__ void __launch_bounds__(kMlpThreads) k_mlp_forward_dense(MlpDev m, const uint16_t* __restrict__ X, int64_t n,
-                                                                   float* __restrict__ y, float* __restrict__ z1) {
-    __shared__ float part[kMlpRows][4];
-    const uint32_t* Xw = reinterpret_cast<const uint32_t*>(X);
-    for (int64_t t0 = static_cast<int64_t>(blockIdx.x) * kMlpRows; t0 < n; t0 += static_cast<int64_t>(gridDim.x) * kMlpRows) {
-        auto a_pair = [&](int r, int k) -> uint32_t {
-            const int64_t row = t0 + r;
-            return row < n ? __ldg(Xw + (row * kMlpIn + k) / 2) : 0u;
-        };
-        auto store_y = [&](int r, float v) {
-            if (t0 + r < n) y[t0 + r] = v;
-        };
-        auto store_z = [&](int r, int c, float v) {
-            if (t0 + r < n) z1[(t0 + r) * kMlpHid + c] = v;
-        };
-        mlp_tile(m, a_pair, store_y, store_z, z1 != nullptr, part);
+// Dense forward on the tensor cores (tcgen05, accumulator in TMEM): one CTA
+// per SM runs 128-row tiles of X; y, and z1 (pre-activations) when asked.
+// A tile whose MMA does not complete within a second gets NaN outputs.
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(MlpDev m, const uint16_t* __restrict__ X,
+                                                                  int64_t n, float* __restrict__ y,
+                                                                  float* __restrict__ z1) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    MlpTcSmem<kMlpIn>& sm = *reinterpret_cast<MlpTcSmem<kMlpIn>*>(smem_raw);
+    tc_setup(sm);
+    tc_stage_w1(sm, m.W1);
+    const int64_t ntiles = (n + kTcRows - 1) / kTcRows;
+    uint32_t phase = 0;
+    const uint4* Xv = reinterpret_cast<const uint4*>(X);
+    const float b2 = __ldg(m.b2);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * kTcRows;
+        for (int i = threadIdx.x; i < kTcRows * (kMlpIn / 8); i += blockDim.x) {
+            const int r = i >> 5, c = i & 31;
+            const int64_t row = r0 + r;
+            const uint4 v = row < n ? __ldg(Xv + row * (kMlpIn / 8) + c) : make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(sm.A + tc::core_offset(r, c * 8, kMlpIn)) = v;
+        }
+        const bool ok = tc_mma_tile(sm, phase);
+        const int r = ((threadIdx.x >> 5) & 3) * 32 + (threadIdx.x & 31);
+        const int h = threadIdx.x >> 7;
+        const int64_t row = r0 + r;
+        if (!ok) {
+            if (h == 0 && row < n) y[row] = __int_as_float(0x7fc00000);
+            break;
+        }
+        float* zr = (z1 != nullptr && row < n) ? z1 + row * kMlpHid : nullptr;
+        const float p = tc_row_half(
+            sm.tmem, m.w2, [&](int c) { return __ldg(m.b1 + c); },
+            [&](int c, float z) {
+                if (zr) zr[c] = z;
+            });
+        sm.part[r][h] = p;
+        __syncthreads();
+        if (threadIdx.x < kTcRows && r0 + static_cast<int64_t>(threadIdx.x) < n)
+            y[r0 + threadIdx.x] = (sm.part[threadIdx.x][0] + sm.part[threadIdx.x][1]) + b2;
     }
+    tc_teardown(sm);
 }
 
 __global__ void k_mlp_features(DevGraph g, const uint32_t* __restrict__ va, const uint32_t* __restrict__ vb, int64_t n,
@@ -191,9 +217,11 @@ extern "C" mhr_status mhr_mlp_forward(const mhr_mlp* m, const uint16_t* X, int64
     MHR_TRY(check_mlp(m));
     if (n < 0 || (n && (!X || !y))) return fail(MHR_EINVAL, "bad forward arguments");
     if (!n) return MHR_OK;
-    const int64_t tiles = (n + kMlpRows - 1) / kMlpRows;
-    const int grid = static_cast<int>(std::min<int64_t>(tiles, std::max(1, device_sm_count()) * 8));
-    k_mlp_forward_dense<<<grid, kMlpThreads, 0, static_cast<cudaStream_t>(cuda_stream)>>>(to_dev(m), X, n, y, z1);
+    const int64_t tiles = (n + kTcRows - 1) / kTcRows;
+    const int grid = static_cast<int>(std::min<int64_t>(tiles, std::max(1, device_sm_count())));
+    const int sb = static_cast<int>(sizeof(MlpTcSmem<kMlpIn>));
+    MHR_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sb));
+    k_mlp_forward_tc<<<grid, kTcThreads, sb, static_cast<cudaStream_t>(cuda_stream)>>>(to_dev(m), X, n, y, z1);
     MHR_CUDA_TRY(cudaGetLastError());
     return MHR_OK;
 }

@@ -45,6 +45,7 @@
 
 #include "mhr_internal.cuh"
 #include "mhr_query.cuh"
+#include "mhr_mlp_tc.cuh"
 #include "mhr_util.cuh"
 
 namespace mhr {
@@ -429,45 +430,78 @@ __global__ void __launch_bounds__(kMlpHid) k_mlp_qbias(const PlanDev* __restrict
 // Learned order (order 2): for every near entry the MLP predicts, from
 // [e_entry; e_far endpoint], the slack of its row bound (best path score
 // through the entry minus the bound); near_bucket orders the rows inside each
-// bound level by it.  Tiles of 32 slots.
-__global__ void __launch_bounds__(kMlpThreads) k_mlp_keys(const PlanDev* __restrict__ P, DevGraph g) {
+// bound level by it.  The endpoint half of the first layer is the per-query
+// bias (k_mlp_qbias), so the tensor cores multiply 128-row tiles of the
+// entries' first 128 features by W1[:, 0:128] (tcgen05, accumulator in TMEM).
+// An MMA that does not complete within a second leaves its tile's predictions
+// at 0 (the order only changes which rows go first, never the result) and
+// counts in kCntTcTimeouts.
+__device__ __forceinline__ uint4 feature_chunk(const DevGraph& g, uint32_t v, int c) {
+    const int k = c * 8;
+    if (g.dtype == MHR_BF16 && (g.d & 7) == 0 && k + 8 <= g.d)
+        return __ldg(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(g.vemb) + static_cast<int64_t>(v) * g.d) + c);
+    return make_uint4(feature_pair(g, v, 0u, k), feature_pair(g, v, 0u, k + 2), feature_pair(g, v, 0u, k + 4),
+                      feature_pair(g, v, 0u, k + 6));
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_keys(const PlanDev* __restrict__ P, DevGraph g) {
     if (P->order != 2) return;
-    __shared__ float part[kMlpRows][4];
-    __shared__ uint32_t va[kMlpRows], vb[kMlpRows];
-    __shared__ int64_t slot[kMlpRows];
-    __shared__ int qrow[kMlpRows];
     const int nq = P->nq;
     const int64_t rows = P->near_off[nq];
-    for (int64_t t0 = static_cast<int64_t>(blockIdx.x) * kMlpRows; t0 < rows; t0 += static_cast<int64_t>(gridDim.x) * kMlpRows) {
-        if (threadIdx.x < kMlpRows) {
+    const int64_t ntiles = (rows + kTcRows - 1) / kTcRows;
+    if (static_cast<int64_t>(blockIdx.x) >= ntiles) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    MlpTcSmem<128>& sm = *reinterpret_cast<MlpTcSmem<128>*>(smem_raw);
+    __shared__ int64_t slot[kTcRows];
+    __shared__ uint32_t va[kTcRows];
+    __shared__ int qrow[kTcRows];
+    tc_setup(sm);
+    tc_stage_w1(sm, P->mlp.W1);
+    uint32_t phase = 0;
+    const float b2 = __ldg(P->mlp.b2);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t t0 = tile * kTcRows;
+        if (threadIdx.x < kTcRows) {
             const int64_t r = t0 + threadIdx.x;
             slot[threadIdx.x] = -1;
-            va[threadIdx.x] = vb[threadIdx.x] = 0u;
+            va[threadIdx.x] = 0u;
+            qrow[threadIdx.x] = 0;
             if (r < rows) {
                 const int q = static_cast<int>(upper_bound_i64(P->near_off, nq + 1, r) - 1);
                 const bool fwd = P->dir[q] == 1;
                 const int64_t base = fwd ? P->a_off[q] : P->totA + P->c_off[q];
                 const int64_t x = base + (r - P->near_off[q]);
-                const ListEnt e = P->list[x];
                 slot[threadIdx.x] = x;
-                va[threadIdx.x] = e.vertex;
-                vb[threadIdx.x] = fwd ? P->T[q] : P->S[q];
+                va[threadIdx.x] = P->list[x].vertex;
                 qrow[threadIdx.x] = q;
             }
         }
         __syncthreads();
-        // the endpoint half of the input is folded into the per-query bias
-        auto a_pair = [&](int r, int k) -> uint32_t { return slot[r] >= 0 ? feature_pair(g, va[r], vb[r], k) : 0u; };
-        auto bias = [&](int r, int c) -> float {
-            return slot[r] >= 0 ? P->mlp_qbias[static_cast<int64_t>(qrow[r]) * kMlpHid + c] : 0.f;
-        };
-        auto store_y = [&](int r, float y) {
+        for (int i = threadIdx.x; i < kTcRows * 16; i += blockDim.x) {
+            const int r = i >> 4, c = i & 15;
+            const uint4 v = slot[r] >= 0 ? feature_chunk(g, va[r], c) : make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(sm.A + tc::core_offset(r, c * 8, 128)) = v;
+        }
+        const bool ok = tc_mma_tile(sm, phase);
+        if (!ok) {
+            if (threadIdx.x < kTcRows && slot[threadIdx.x] >= 0) P->mlp_pred[slot[threadIdx.x]] = 0.f;
+            if (threadIdx.x == 0) atomicAdd(&P->counters[kCntTcTimeouts], 1ull);
+            break;
+        }
+        const int r = ((threadIdx.x >> 5) & 3) * 32 + (threadIdx.x & 31);
+        const int h = threadIdx.x >> 7;
+        const float* qb = P->mlp_qbias + static_cast<int64_t>(qrow[r]) * kMlpHid;
+        const float p = tc_row_half(
+            sm.tmem, P->mlp.w2, [&](int c) { return qb[c]; }, [&](int, float) {});
+        sm.part[r][h] = p;
+        __syncthreads();
+        if (threadIdx.x < kTcRows && slot[threadIdx.x] >= 0) {
             // the predicted slack of the row bound (a path can only score below it)
-            if (slot[r] >= 0) P->mlp_pred[slot[r]] = fminf(y, 0.f);
-        };
-        auto store_z = [&](int, int, float) {};
-        mlp_tile_k<kMlpIn / 32>(P->mlp, a_pair, bias, store_y, store_z, false, part);
+            const float y = (sm.part[threadIdx.x][0] + sm.part[threadIdx.x][1]) + b2;
+            P->mlp_pred[slot[threadIdx.x]] = fminf(y, 0.f);
+        }
     }
+    tc_teardown(sm);
 }
 
 // row bound of every near entry, its order key and the per-query key range
@@ -1481,42 +1515,60 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u)
                 if (valid[u]) xv[u] = __ldg(colsrc + epos[u]);
+            // Membership of the UNROLL groups' far vertices, in passes whose
+            // loads do not depend on one another across groups, so a warp has
+            // all of them in flight at once: bitmap bit and rank (shared
+            // memory), then for a coarse bitmap the start of the set bit's run
+            // in the far list and the first far vertex of that run (global),
+            // then the rare walk along the run.
+            bool hit[UNROLL];
+            uint32_t fk[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                hit[u] = false;
+                fk[u] = 0;
+                if (valid[u]) {
+                    const uint32_t x = xv[u];
+                    const uint32_t bv = x >> sigma;
+                    if ((sm.bm[bv >> 5] >> (bv & 31u)) & 1u) {
+                        hit[u] = true;
+                        // exact bitmap: the rank of x is its far-list index
+                        fk[u] = bm_rank(sm, sigma == 0 ? x : bv);
+                    }
+                }
+            }
+            if (sigma > 0) {
+                // coarse bitmap: the set bit's run in the far list starts at far_start[rank]
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u)
+                    if (hit[u]) fk[u] = __ldg(far_start + fk[u]);
+                uint32_t fv[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) fv[u] = hit[u] ? far[fk[u]].vertex : 0u;
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    if (!hit[u]) continue;
+                    const uint32_t x = xv[u];
+                    uint32_t k = fk[u], v = fv[u];
+                    while (v < x && ++k < static_cast<uint32_t>(far_cnt)) v = far[k].vertex;
+                    hit[u] = k < static_cast<uint32_t>(far_cnt) && v == x;
+                    fk[u] = k;
+                }
+            }
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
                 const int gidx = gb + u;
                 if (gidx >= ngroups) break;
-                bool hit = false;
-                uint32_t fk = 0;
-                if (valid[u]) {
-                    const uint32_t x = xv[u];
-                    const uint32_t bv = x >> sigma;
-                    const uint32_t word = sm.bm[bv >> 5];
-                    if ((word >> (bv & 31u)) & 1u) {
-                        if (sigma == 0) {
-                            // exact bitmap: the rank of x is its far-list index
-                            fk = bm_rank(sm, x);
-                            hit = true;
-                        } else {
-                            // coarse bitmap: walk the run of the set bit in the far list
-                            int k = static_cast<int>(far_start[bm_rank(sm, bv)]);
-                            while (k < far_cnt && far[k].vertex < x) ++k;
-                            if (k < far_cnt && far[k].vertex == x) {
-                                fk = static_cast<uint32_t>(k);
-                                hit = true;
-                            }
-                        }
-                    }
-                }
-                const unsigned b = __ballot_sync(FULL, hit);
+                const unsigned b = __ballot_sync(FULL, hit[u]);
                 if (b) {
                     int base = 0;
                     const int leader = __ffs(b) - 1;
                     if (lane == leader) base = atomicAdd(&sm.hit_cnt, __popc(b));
                     base = __shfl_sync(FULL, base, leader);
-                    if (hit) {
+                    if (hit[u]) {
                         Hit h;
                         h.near_k = nk[u];
-                        h.far_k = fk;
+                        h.far_k = fk[u];
                         h.epos = epos[u];
                         hits[base + __popc(b & lanemask_lt())] = h;
                     }
@@ -2433,7 +2485,7 @@ static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int
         k_plan<<<1, 1024, 0, st>>>(d);
         k_order_key<<<sms * 4, 256, 0, st>>>(d, g);
         k_mlp_qbias<<<std::min(p->nq, sms * 4), kMlpHid, 0, st>>>(d, g);
-        k_mlp_keys<<<sms * 8, kMlpThreads, 0, st>>>(d, g);
+        k_mlp_keys<<<sms, kTcThreads, sizeof(MlpTcSmem<128>), st>>>(d, g);
         k_order_hist<<<sms * 4, 256, 0, st>>>(d);
         const int64_t* nH = reinterpret_cast<const int64_t*>(p->dregion + offsetof(PlanDev, nhist));
         e = device_excl_scan<uint32_t>(p->h.hist, nH, p->h.partials, p->h.hscan, st);
@@ -2621,6 +2673,9 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precisio
             p->expand_per_sm = nb;
         cudaGetLastError();
     }
+    e = cudaFuncSetAttribute(k_mlp_keys, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(sizeof(MlpTcSmem<128>)));
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaFuncSetAttribute (ordering MLP)"));
     e = cudaFuncSetAttribute(k_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(exact_smem_bytes()));
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaFuncSetAttribute (exact)"));

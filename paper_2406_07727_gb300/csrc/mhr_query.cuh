@@ -65,6 +65,7 @@ enum {
     kCntSeed = 8,
     kCntSkippedItems = 9,
     kCntLabels = 10,
+    kCntTcTimeouts = 11,  // ordering-MLP tiles whose tensor-core MMA gave up waiting
     kCntCount = 16
 };
 
