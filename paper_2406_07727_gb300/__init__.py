@@ -48,6 +48,7 @@ from ._mhr import (  # noqa: F401
     mhr_tail_topk,
     tails_from_device,
     mhr_beam_paths,
+    beams_from_device,
     BEAM_DTYPE,
 )
 

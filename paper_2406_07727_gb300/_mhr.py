@@ -480,20 +480,39 @@ def mhr_tail_topk(g: Graph, H, Rq, K: int, cand_type: int = -1, out=None, n_out=
     return out, n_out
 
 
-def mhr_beam_paths(g: Graph, S, T, H: int, K: int, stream=None, with_stats: bool = False):
+def mhr_beam_paths(g: Graph, S, T, H: int, K: int, out=None, n_out=None, stream=None, with_stats: bool = False):
     """Generic H-hop search with a per-path beam of width K (Alg. 6 / Alg. 7):
     the K best s->t paths of at most H hops the beam reaches, per query.  Host
-    arrays in, host arrays out (out [nq, K] of BEAM_DTYPE, n_out [nq]);
-    synchronous."""
+    arrays in -> host arrays out (out [nq, K] of BEAM_DTYPE, n_out [nq]);
+    device tensors in -> device tensors out (a uint8 tensor [nq, K*64] and an
+    int32 tensor [nq]).  Synchronous."""
     lib = load_library()
-    S, T = _host(S, np.uint32), _host(T, np.uint32)
+    mem = _mem_of(S, T, out, n_out)
     nq = int(S.shape[0])
-    out = np.zeros((nq, max(int(K), 1)), dtype=BEAM_DTYPE)
-    n_out = np.zeros(nq, dtype=np.int32)
+    if mem == MHR_MEM_HOST:
+        S, T = _host(S, np.uint32), _host(T, np.uint32)
+        if out is None:
+            out = np.zeros((nq, max(int(K), 1)), dtype=BEAM_DTYPE)
+        if n_out is None:
+            n_out = np.zeros(nq, dtype=np.int32)
+    else:
+        import torch
+        if out is None:
+            out = torch.empty((nq, max(int(K), 1) * BEAM_DTYPE.itemsize), dtype=torch.uint8, device=S.device)
+        if n_out is None:
+            n_out = torch.empty(nq, dtype=torch.int32, device=S.device)
     st = Stats()
     _check(lib.mhr_beam_paths(g.handle, nq, _ptr(S), _ptr(T), int(H), int(K), _ptr(out), _ptr(n_out),
-                              MHR_MEM_HOST, ctypes.byref(st) if with_stats else None, _stream_ptr(stream)))
+                              mem, ctypes.byref(st) if with_stats else None, _stream_ptr(stream)))
     return (out, n_out, st.as_dict()) if with_stats else (out, n_out)
+
+
+def beams_from_device(buf, K: int) -> np.ndarray:
+    """uint8 device/host buffer [nq, K*64] -> structured numpy array [nq, K]."""
+    if hasattr(buf, "cpu"):
+        buf = buf.cpu().numpy()
+    buf = np.ascontiguousarray(buf)
+    return buf.view(BEAM_DTYPE).reshape(buf.shape[0], K)
 
 
 def tails_from_device(buf, K: int) -> np.ndarray:

@@ -870,10 +870,10 @@ __device__ void setup_query(MidSmem& sm, const PlanDev* __restrict__ P, int q) {
         // coarse bitmap (2^sigma vertices per bit): the far list is sorted by
         // vertex, so the vertices of a set bit are contiguous in it; record
         // where the run of each set bit starts, indexed by the bit's rank
-        uint32_t* fs = P->far_start + static_cast<int64_t>(blockIdx.x) * P->far_cap;
+        uint2* fs = P->far_start + static_cast<int64_t>(blockIdx.x) * P->far_cap;
         for (int k = threadIdx.x; k < sm.far_cnt; k += blockDim.x) {
-            const uint32_t bv = far[k].vertex >> sigma;
-            if (k == 0 || (far[k - 1].vertex >> sigma) != bv) fs[bm_rank(sm, bv)] = static_cast<uint32_t>(k);
+            const uint32_t fv = far[k].vertex, bv = fv >> sigma;
+            if (k == 0 || (far[k - 1].vertex >> sigma) != bv) fs[bm_rank(sm, bv)] = make_uint2(static_cast<uint32_t>(k), fv);
         }
         __syncthreads();
     }
@@ -1445,7 +1445,8 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         const uint32_t* colsrc = sm.dir ? g.col : g.rcol;
         const ListEnt* far = P->list + sm.far_base;
         const int far_cnt = sm.far_cnt;
-        const uint32_t* far_start = P->far_start + static_cast<int64_t>(blockIdx.x) * P->far_cap;
+        const uint2* far_start = P->far_start + static_cast<int64_t>(blockIdx.x) * P->far_cap;
+        const uint16_t* relsrc = sm.dir ? g.rel : g.rrel;
         MHR_WSTART();
         for (int gb = warp * UNROLL; gb < ngroups; gb += kMidWarps * UNROLL) {
             MHR_SUB_START();
@@ -1470,13 +1471,14 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                     }
                 }
             }
-            uint32_t xv[UNROLL], epos[UNROLL], nk[UNROLL];
+            uint32_t xv[UNROLL], rv[UNROLL], epos[UNROLL], nk[UNROLL];
             bool valid[UNROLL];
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
                 const int gidx = gb + u;
                 valid[u] = false;
                 xv[u] = 0;
+                rv[u] = 0;
                 epos[u] = 0;
                 nk[u] = 0;
                 if (gidx < ngroups) {
@@ -1512,9 +1514,13 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                 }
             }
             MHR_SUB(0);
+            // far vertex and relation of every edge (the relation travels with a hit)
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u)
-                if (valid[u]) xv[u] = __ldg(colsrc + epos[u]);
+                if (valid[u]) {
+                    xv[u] = __ldg(colsrc + epos[u]);
+                    rv[u] = __ldg(relsrc + epos[u]);
+                }
             // Membership of the UNROLL groups' far vertices, in passes whose
             // loads do not depend on one another across groups, so a warp has
             // all of them in flight at once: bitmap bit and rank (shared
@@ -1539,12 +1545,18 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
             }
             if (sigma > 0) {
                 // coarse bitmap: the set bit's run in the far list starts at far_start[rank]
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u)
-                    if (hit[u]) fk[u] = __ldg(far_start + fk[u]);
+                // (written by this CTA's query set-up: a coherent load), which also
+                // holds the run's first vertex
                 uint32_t fv[UNROLL];
 #pragma unroll
-                for (int u = 0; u < UNROLL; ++u) fv[u] = hit[u] ? far[fk[u]].vertex : 0u;
+                for (int u = 0; u < UNROLL; ++u) {
+                    fv[u] = 0u;
+                    if (hit[u]) {
+                        const uint2 st = far_start[fk[u]];
+                        fk[u] = st.x;
+                        fv[u] = st.y;
+                    }
+                }
 #pragma unroll
                 for (int u = 0; u < UNROLL; ++u) {
                     if (!hit[u]) continue;
@@ -1569,7 +1581,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                         Hit h;
                         h.near_k = nk[u];
                         h.far_k = fk[u];
-                        h.epos = epos[u];
+                        h.r2 = rv[u];
                         hits[base + __popc(b & lanemask_lt())] = h;
                     }
                 }
@@ -1590,7 +1602,6 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         // A warp takes batches of 32 hits: one lane loads each hit's frontier
         // entries, then groups of G lanes score H = 32 / G hits at a time over
         // G rounds, so every warp keeps H hits' embedding rows in flight.
-        const uint16_t* relsrc = sm.dir ? g.rel : g.rrel;
         const ListEnt* nearL = P->nearL + sm.near_base;  // ordered position
         const float* w1s = P->w32 + sm.a_base;
         const float* w3s = P->w32 + sm.c_base;
@@ -1601,7 +1612,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         unsigned pend = 0;         // lanes whose hit still has combinations to expand
         uint32_t slice = 0;        // this lane's next combination
         uint32_t hu = 0, hv = 0, hr2 = 0, has = 0, hal = 0, hcs = 0, hcl = 0, hnk = 0;
-        float hw2 = 0.f;
+        float hw2 = 0.f, hm1 = 0.f, hm3 = 0.f;  // middle-edge weight; run maxima of the hit's u and v
         NearRow nrow;
         nrow.id = 0xffffffffu;
         for (;;) {
@@ -1642,7 +1653,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                             const ListEnt& ec = sm.dir ? fe : ne;  // hop-3 side (v)
                             hu = ea.vertex;
                             hv = ec.vertex;
-                            hr2 = relsrc[ht.epos];
+                            hr2 = ht.r2;
                             has = ea.run_start;
                             hal = ea.run_len;
                             hcs = ec.run_start;
@@ -1711,6 +1722,8 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                             if (lane / H == r) w2m = tw;
                         }
                         hw2 = w2m;
+                        hm1 = mw1;
+                        hm3 = mw3;
                         // a hit with no combination (disallowed middle relation) stays out
                         if (hal == 0u) hw2 = neg_inf();
                         MHR_SUB(3);
@@ -1726,8 +1739,33 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                     // sequence that the warp walks 32 at a time, so a hit with many
                     // parallel edges does not serialise the warp.
                     bool stop = false;
-                    {
-                        const bool mine = (pend >> lane) & 1u;
+                    const bool mine0 = (pend >> lane) & 1u;
+                    if (__all_sync(FULL, !mine0 || (hal * hcl == 1u && slice == 0u))) {
+                        // Every pending hit has one combination (runs of one edge on both
+                        // sides, the common case): its path score is the hit's smax, which
+                        // already passed the threshold.  One candidate per pending lane.
+                        const int np = __popc(pend);
+                        if (used + np > budget) {
+                            stop = true;
+                        } else if (np) {
+                            int base = 0;
+                            const int leader = __ffs(pend) - 1;
+                            if (lane == leader) base = atomicAdd(&sm.cand_cnt, np);
+                            base = __shfl_sync(FULL, base, leader);
+                            if (mine0) {
+                                Cand cd;
+                                cd.s32 = __fadd_rn(__fadd_rn(hm1, hw2), hm3);
+                                cd.a_idx = has;
+                                cd.c_idx = hcs;
+                                cd.r2 = static_cast<uint16_t>(hr2);
+                                cd.pad = 0;
+                                sm.cand[base + __popc(pend & lanemask_lt())] = cd;
+                            }
+                            used += np;
+                            pend = 0u;
+                        }
+                    } else {
+                        const bool mine = mine0;
                         const uint32_t ncomb = hal * hcl;
                         const uint32_t rem = mine ? ncomb - slice : 0u;
                         uint32_t incl = rem;
@@ -1755,6 +1793,10 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                             const uint32_t o_hcs = __shfl_sync(FULL, hcs, own);
                             const uint32_t o_r2 = __shfl_sync(FULL, hr2, own);
                             const float o_w2 = __shfl_sync(FULL, hw2, own);
+                            // a run of one edge: its weight is the run's maximum (no slot load)
+                            const uint32_t o_hal = __shfl_sync(FULL, hal, own);
+                            const float o_m1 = __shfl_sync(FULL, hm1, own);
+                            const float o_m3 = __shfl_sync(FULL, hm3, own);
                             bool keep = false;
                             Cand cd;
                             if (f < total) {
@@ -1764,7 +1806,9 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                                     i = sl / o_hcl;
                                     j = sl - i * o_hcl;
                                 }
-                                const float s32 = __fadd_rn(__fadd_rn(w1s[o_has + i], o_w2), w3s[o_hcs + j]);
+                                const float w1 = o_hal == 1u ? o_m1 : w1s[o_has + i];
+                                const float w3 = o_hcl == 1u ? o_m3 : w3s[o_hcs + j];
+                                const float s32 = __fadd_rn(__fadd_rn(w1, o_w2), w3);
                                 // -inf: a slot of a disallowed relation (constrained queries)
                                 keep = s32 >= thr && s32 != neg_inf();
                                 cd.s32 = s32;
@@ -2440,14 +2484,14 @@ static mhr_status ensure_far(Plan* p, int64_t cap) {
     if (cap <= p->h.far_cap && p->h.far_start) return MHR_OK;
     cap = std::max(cap, 2 * p->h.far_cap);
     void* mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, sizeof(uint32_t) * static_cast<size_t>(cap) * p->grid);
+    cudaError_t e = cudaMalloc(&mem, sizeof(uint2) * static_cast<size_t>(cap) * p->grid);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (far-set run starts)");
     if (p->far_mem) {
         cudaDeviceSynchronize();
         cudaFree(p->far_mem);
     }
     p->far_mem = mem;
-    p->h.far_start = static_cast<uint32_t*>(mem);
+    p->h.far_start = static_cast<uint2*>(mem);
     p->h.far_cap = cap;
     return MHR_OK;
 }

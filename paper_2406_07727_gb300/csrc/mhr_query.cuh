@@ -36,7 +36,7 @@ static_assert(sizeof(Cand) == 16, "Cand is 16 bytes");
 struct Hit {
     uint32_t near_k;
     uint32_t far_k;
-    uint32_t epos;  // CSR position of the middle edge (relation id lookup)
+    uint32_t r2;  // relation id of the middle edge
 };
 
 // one distinct frontier vertex of a query
@@ -147,7 +147,8 @@ struct PlanDev {
     unsigned long long* counters;  // kCntCount
     unsigned long long* cursors;   // [grid] next item of each CTA's own range
     uint32_t* drained;             // [(grid + 31) / 32] bit v: range v has no item left
-    uint32_t* far_start;           // [grid x far_cap] coarse bitmap: far-list start of each set bit's run
+    uint2* far_start;              // [grid x far_cap] coarse bitmap: (far-list start, its vertex) of
+                                   // each set bit's run
     int64_t far_cap;               // longest far list of the batch (coarse bitmaps only)
     int64_t* partials;             // scan scratch
 };

@@ -671,13 +671,22 @@ ScanKernel pick_scan(const DevGraph& dg) {
     return k;
 }
 
-mhr_status launch_scan(const mhr_graph* g, const ScanKernel& sk, const ScanArgs& a, cudaStream_t st) {
+// Host-side set-up of the scan kernel for launches of up to nq_max queries:
+// the shared-memory attribute and the resident blocks per SM.  Done once per
+// call, before any event is recorded, so event times cover device work only.
+mhr_status scan_setup(const mhr_graph* g, const ScanKernel& sk, int nq_max, int* per_sm) {
+    const size_t smem = static_cast<size_t>(nq_max) * g->dg.d * 4 + static_cast<size_t>(nq_max) * 4;
+    MHR_CUDA_TRY(cudaFuncSetAttribute(sk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    int n = 0;
+    MHR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sk.fn, kScanThreads, smem));
+    *per_sm = std::max(1, n);
+    return MHR_OK;
+}
+
+// a.nq <= the nq_max given to scan_setup, whose per_sm this takes
+mhr_status launch_scan(const mhr_graph* g, const ScanKernel& sk, const ScanArgs& a, int per_sm, cudaStream_t st) {
     if (a.nq <= 0 || a.n_visit <= 0) return MHR_OK;
     const size_t smem = static_cast<size_t>(a.nq) * g->dg.d * 4 + static_cast<size_t>(a.nq) * 4;
-    MHR_CUDA_TRY(cudaFuncSetAttribute(sk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    int per_sm = 0;
-    MHR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk.fn, kScanThreads, smem));
-    per_sm = std::max(1, per_sm);
     const int cpw = sk.rows_per_group * (32 / sk.G);
     const int64_t ntiles = (a.n_visit + cpw - 1) / cpw;
     const int64_t need = (ntiles + kScanWarps - 1) / kScanWarps;
@@ -823,6 +832,8 @@ extern "C" mhr_status mhr_tail_topk(const mhr_graph* gc, int32_t nq, const uint3
     const ScanKernel sk = pick_scan(g->dg);
     const size_t final_smem = sizeof(BandRec) * kSortMax + (d <= kQ64Max ? sizeof(double) * d : 0);
     MHR_CUDA_TRY(cudaFuncSetAttribute(k_tail_final, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(final_smem)));
+    int per_sm = 1;
+    MHR_TRY(scan_setup(g, sk, std::min(QB, nq), &per_sm));
 
     int64_t n_pairs = 0, n_surv = 0, n_band = 0, n_rescan = 0;
     double ms_scan = 0.0;
@@ -845,7 +856,7 @@ extern "C" mhr_status mhr_tail_topk(const mhr_graph* gc, int32_t nq, const uint3
             a.surv = d_sa;
             a.cap = capA;
             a.cnt = d_cnt;
-            MHR_TRY(launch_scan(g, sk, a, st));
+            MHR_TRY(launch_scan(g, sk, a, per_sm, st));
             k_tail_thr<<<qb, kFinalThreads, 0, st>>>(d_sa, capA, d_cnt, K, E2, d_thr);
             MHR_CUDA_TRY(cudaGetLastError());
             n_pairs += static_cast<int64_t>(qb) * M;
@@ -857,7 +868,7 @@ extern "C" mhr_status mhr_tail_topk(const mhr_graph* gc, int32_t nq, const uint3
         a.cap = capB;
         a.cnt = cntB;
         MHR_CUDA_TRY(cudaEventRecord(tc->ev[2], st));
-        MHR_TRY(launch_scan(g, sk, a, st));
+        MHR_TRY(launch_scan(g, sk, a, per_sm, st));
         MHR_CUDA_TRY(cudaEventRecord(tc->ev[3], st));
         n_pairs += static_cast<int64_t>(qb) * Nc;
         k_tail_final<<<qb, kFinalThreads, final_smem, st>>>(g->dg, d_h + c0, d_r + c0, d_sb, capB, cntB, d_band, K, E2,
@@ -892,7 +903,7 @@ extern "C" mhr_status mhr_tail_topk(const mhr_graph* gc, int32_t nq, const uint3
             b.surv = bs;
             b.cap = Nc;
             b.cnt = bcnt;
-            MHR_TRY(launch_scan(g, sk, b, st));
+            MHR_TRY(launch_scan(g, sk, b, per_sm, st));
             k_tail_final<<<1, kFinalThreads, final_smem, st>>>(g->dg, d_h + c0 + i, d_r + c0 + i, bs, Nc, bcnt, bb, K, E2,
                                                                d_out + static_cast<int64_t>(c0 + i) * K, d_nout + c0 + i,
                                                                d_bc + i);

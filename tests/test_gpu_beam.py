@@ -72,3 +72,31 @@ def test_argument_errors(mhr):
             mhr.mhr_beam_paths(G, S, S, 3, 5)
     finally:
         G.close()
+
+
+def test_device_arrays(mhr):
+    """Queries and results as device arrays (MHR_MEM_DEVICE): the caller's
+    device pointers are used directly; results equal the oracle's and the
+    host-array call's."""
+    import torch
+    rng = np.random.default_rng(12)
+    g = random_kg(rng, 300, 6000, 5, 16, scale=0.3)
+    S = rng.integers(0, g.n, size=10).astype(np.uint32)
+    T = ((S + 1 + rng.integers(0, g.n - 1, size=10)) % g.n).astype(np.uint32)
+    H, K = 3, 8
+    G = mhr.load_kg(g)
+    try:
+        dS = torch.from_numpy(S.view(np.int32)).cuda()
+        dT = torch.from_numpy(T.view(np.int32)).cuda()
+        out, n_out = mhr.mhr_beam_paths(G, dS, dT, H, K)
+        assert out.is_cuda and n_out.is_cuda
+        host, n_host = mhr.mhr_beam_paths(G, S, T, H, K)
+    finally:
+        G.close()
+    dev = mhr.beams_from_device(out, K)
+    dn = n_out.cpu().numpy()
+    assert np.array_equal(dn, n_host)
+    for q in range(len(S)):
+        assert dev[q][: dn[q]].tobytes() == host[q][: n_host[q]].tobytes()
+        want = tuples(oracle.beam_paths(g, int(S[q]), int(T[q]), H, K), K)
+        assert tuples(dev[q], int(dn[q])) == want, q
