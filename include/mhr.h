@@ -159,11 +159,19 @@ typedef struct {
     const mhr_mlp* mlp;  /* order == 2 only */
     int32_t tile;        /* 32-edge groups each warp of the middle join scans per step:
                             0 = default (4), else 4 or 8 (MHR_EINVAL otherwise) */
-    int32_t reserved;
+    int32_t part_count;  /* vertex partition of the paths (the multi-GPU form of Sec. 3.3's
+                            partitioned work): with part_count >= 2 only the paths whose
+                            hop-1 vertex u has u % part_count == part_index are searched, so
+                            part_count calls (one per GPU) cover every path exactly once and
+                            mhr_merge_paths of their lists is the unpartitioned result.
+                            0 or 1 = every path.  MHR_EINVAL unless 0 <= part_index <
+                            part_count.  Not with mhr_training_labels. */
     const mhr_constraints* constraints;  /* NULL = unconstrained; see mhr_constraints.  The
                             work counters then count the combinations of allowed hop-1 and
                             hop-3 vertices and allowed middle edges, before the hop-1 and
                             hop-3 relation filter.  Not with mhr_training_labels. */
+    int32_t part_index;  /* see part_count */
+    int32_t reserved;
 } mhr_query_opts;
 
 /* Work counters of the last call (optional output). */
@@ -249,6 +257,26 @@ mhr_status mhr_topk_paths_batched(const mhr_graph* g, int32_t nq, const uint32_t
                                   const uint32_t* t, int32_t K, mhr_path* out, int32_t* n_out,
                                   mhr_mem mem, const mhr_query_opts* opts, mhr_stats* stats,
                                   void* cuda_stream);
+
+/*
+ * Merge of partial top-K lists (Alg. 2, ReduceTopKTree: the per-thread K-best
+ * lists are merged pairwise in a tree).  Here the lists are the results of
+ * disjoint path sets of the same queries -- the parts of a vertex-partitioned
+ * search (mhr_query_opts.part_count), one per GPU -- and the merge runs on the
+ * GPU: log2(n_parts) rounds, each merging pairs of lists by the result order
+ * (score descending, then (u, r1, v, r2, r3) ascending; every list must
+ * already be in that order, as the search returns it) and keeping the first K.
+ *   parts   n_parts * nq * K paths: part p, query i at parts[(p * nq + i) * K]
+ *   n_parts_out  n_parts * nq counts (part p, query i at [p * nq + i]); -1
+ *           (an invalid query) in any part makes the output count -1
+ *   out     nq * K paths; n_out[i] = min(K, sum of the parts' counts)
+ *   mem     where parts, n_parts_out, out and n_out live
+ * The parts must not share a path (the result would repeat it).  Host
+ * memory: synchronous.  Device memory: asynchronous on cuda_stream.
+ * MHR_EINVAL on NULL pointers, nq < 0, n_parts < 1, K outside [1, MHR_K_MAX].
+ */
+mhr_status mhr_merge_paths(int32_t nq, int32_t K, int32_t n_parts, const mhr_path* parts, const int32_t* n_parts_out,
+                           mhr_path* out, int32_t* n_out, mhr_mem mem, void* cuda_stream);
 
 /*
  * Launch-shape autotuner for the batched search (the paper has no

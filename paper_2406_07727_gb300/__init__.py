@@ -48,10 +48,12 @@ from ._mhr import (  # noqa: F401
     mhr_tail_topk,
     tails_from_device,
     mhr_beam_paths,
+    mhr_merge_paths,
     beams_from_device,
     BEAM_DTYPE,
 )
 
 from .learn import OrderingMLP, train_ordering_mlp  # noqa: E402,F401
+from .partition import topk_paths_partitioned  # noqa: E402,F401
 
 load_library()

@@ -70,8 +70,9 @@ class Constraints(ctypes.Structure):
 class QueryOpts(ctypes.Structure):
     _fields_ = [("chunk", ctypes.c_int32), ("order", ctypes.c_int32), ("prune", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("mlp", ctypes.POINTER(MLP)),
-                ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("constraints", ctypes.POINTER(Constraints))]
+                ("tile", ctypes.c_int32), ("part_count", ctypes.c_int32),
+                ("constraints", ctypes.POINTER(Constraints)), ("part_index", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -100,7 +101,8 @@ class GraphInfo(ctypes.Structure):
 EXPORTS = ("mhr_graph_load", "mhr_graph_free", "mhr_graph_get_info", "mhr_edge_scores", "mhr_topk_paths",
            "mhr_topk_paths_batched", "mhr_topk_paths_noalloc", "mhr_training_labels",
            "mhr_mlp_features", "mhr_mlp_forward", "mhr_mlp_backward", "mhr_mlp_adam",
-           "mhr_mlp_to_bf16", "mhr_tail_topk", "mhr_beam_paths", "mhr_last_error", "mhr_version")
+           "mhr_mlp_to_bf16", "mhr_tail_topk", "mhr_beam_paths", "mhr_merge_paths", "mhr_last_error",
+           "mhr_version")
 
 _lock = threading.Lock()
 _lib = None
@@ -160,6 +162,8 @@ def load_library(build_if_missing: bool = True):
         lib.mhr_tail_topk.argtypes = [P, i32, P, P, i32, i32, P, P, ctypes.c_int, ctypes.POINTER(Stats), P]
         lib.mhr_beam_paths.restype = ctypes.c_int
         lib.mhr_beam_paths.argtypes = [P, i32, P, P, i32, i32, P, P, ctypes.c_int, ctypes.POINTER(Stats), P]
+        lib.mhr_merge_paths.restype = ctypes.c_int
+        lib.mhr_merge_paths.argtypes = [i32, i32, i32, P, P, P, P, ctypes.c_int, P]
         lib.mhr_last_error.restype = ctypes.c_char_p
         lib.mhr_last_error.argtypes = []
         lib.mhr_version.restype = ctypes.c_char_p
@@ -409,6 +413,33 @@ def mhr_topk_paths_batched(g: Graph, S, T, K: int, out=None, n_out=None, opts=No
     _check(rc)
     if with_stats:
         return out, n_out, st.as_dict()
+    return out, n_out
+
+
+def mhr_merge_paths(parts, n_parts_out, K: int, out=None, n_out=None, stream=None):
+    """Tree merge (Alg. 2) of the partial top-K lists of disjoint path sets:
+    parts [n_parts, nq, K] of PATH_DTYPE (or a uint8 device tensor
+    [n_parts, nq, K*24]) with counts n_parts_out [n_parts, nq]; returns the
+    first K of every query's merged order and the counts.  Host arrays in ->
+    host arrays out (synchronous); device tensors in -> device tensors out."""
+    lib = load_library()
+    mem = _mem_of(parts, n_parts_out, out, n_out)
+    n_parts, nq = int(n_parts_out.shape[0]), int(n_parts_out.shape[1])
+    if mem == MHR_MEM_HOST:
+        parts = np.ascontiguousarray(parts, dtype=PATH_DTYPE)
+        n_parts_out = _host(n_parts_out, np.int32)
+        if out is None:
+            out = np.zeros((nq, int(K)), dtype=PATH_DTYPE)
+        if n_out is None:
+            n_out = np.zeros(nq, dtype=np.int32)
+    else:
+        import torch
+        if out is None:
+            out = torch.empty((nq, int(K) * PATH_DTYPE.itemsize), dtype=torch.uint8, device=parts.device)
+        if n_out is None:
+            n_out = torch.empty(nq, dtype=torch.int32, device=parts.device)
+    _check(lib.mhr_merge_paths(nq, int(K), n_parts, _ptr(parts), _ptr(n_parts_out), _ptr(out), _ptr(n_out), mem,
+                               _stream_ptr(stream)))
     return out, n_out
 
 

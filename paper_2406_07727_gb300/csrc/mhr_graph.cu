@@ -18,7 +18,7 @@
 
 static_assert(sizeof(mhr_graph_desc) == 104, "mhr_graph_desc layout");
 static_assert(sizeof(mhr_path) == 24, "mhr_path layout");
-static_assert(sizeof(mhr_query_opts) == 40, "mhr_query_opts layout");
+static_assert(sizeof(mhr_query_opts) == 48, "mhr_query_opts layout");
 static_assert(sizeof(mhr_constraints) == 40, "mhr_constraints layout");
 static_assert(sizeof(mhr_graph_info) == 80, "mhr_graph_info layout");
 static_assert(sizeof(mhr_mlp) == 32, "mhr_mlp layout");

@@ -257,6 +257,10 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, D
             // A vertex with no scan edges can neither be scanned nor be hit, so it
             // never lies on a path: it is dropped from the distinct list.
             bool head = !excl && sdeg > 0 && (k == 0 || prev != vtx);
+            // vertex partition: this call owns the paths whose hop-1 vertex u it owns
+            if (sideA && P->part_count > 1 && vtx % static_cast<uint32_t>(P->part_count) !=
+                                                  static_cast<uint32_t>(P->part_index))
+                head = false;
             bool allowed = true;
             const uint8_t* cons = P->cons;
             if (cons) {
@@ -2819,6 +2823,13 @@ static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint
     }
     p->h.label = label ? 1 : 0;
     if (label && (p->h.prune || p->h.order)) return fail(MHR_EINVAL, "label runs use the plain search");
+    // vertex partition of the paths by their hop-1 vertex
+    p->h.part_count = opts ? opts->part_count : 0;
+    p->h.part_index = opts ? opts->part_index : 0;
+    if (p->h.part_count < 0 || (p->h.part_count > 1 && (p->h.part_index < 0 || p->h.part_index >= p->h.part_count)) ||
+        (p->h.part_count <= 1 && p->h.part_index != 0))
+        return fail(MHR_EINVAL, "opts->part_index must be in [0, part_count)");
+    if (label && p->h.part_count > 1) return fail(MHR_EINVAL, "label runs use the unpartitioned search");
     // constraint flags (Sec. 3.1 query shape), copied with the call's queries
     p->h.cons = nullptr;
     if (opts && opts->constraints) {

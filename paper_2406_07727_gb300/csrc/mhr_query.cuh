@@ -83,6 +83,7 @@ struct PlanDev {
     // constrained query: flags [rel1: R][rel2: R][rel3: R][types of u: 256][types of v: 256]
     // (nonzero = allowed), or NULL when the call has no constraint
     const uint8_t* cons;
+    int32_t part_count, part_index;  // vertex partition: hop-1 vertices u with u % count == index
     MlpDev mlp;            // order 2 weights
     int64_t nhist;        // nq * 256 order buckets
     int64_t item_cap;     // capacity of item_ub

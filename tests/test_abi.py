@@ -43,7 +43,7 @@ def test_struct_layouts():
     assert m.PATH_DTYPE.itemsize == 24
     assert m.TAIL_DTYPE.itemsize == 16
     assert ctypes.sizeof(_mhr.GraphDesc) == 104
-    assert ctypes.sizeof(_mhr.QueryOpts) == 40
+    assert ctypes.sizeof(_mhr.QueryOpts) == 48
     assert ctypes.sizeof(_mhr.Constraints) == 40
     assert ctypes.sizeof(_mhr.GraphInfo) == 80
     assert ctypes.sizeof(_mhr.Stats) == 80
