@@ -93,7 +93,12 @@ KERNELS_PER_STEP = 22
 # 4,869,632 written, learned-ordered form on the medium workload, 16,384-edge
 # items, tile 4; the seed launch adds about 17 MB.  Kept only for that exact
 # configuration.
-TRAFFIC_NCU = {("medium", "chosen", 16384, 4): 99_392_000}
+TRAFFIC_NCU = {("medium", "chosen", 16384, 4): 99_392_000,
+               # batching workload, main join launch of the second call, one
+               # capture each of the current kernel (1 pass: dram__bytes_read.sum
+               # + dram__bytes_write.sum at full size)
+               ("batching", "chosen", 16384, 4): 89_140_000_000,
+               ("batching", "bound", 16384, 4): 89_450_000_000}
 
 
 def dist_env():
@@ -686,6 +691,11 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if sampler:
             sampler.start()
+        # --profile-range: the headline form's timed steps form the profiler
+        # range (ncu --profile-from-start off captures exactly those launches)
+        prof = bool(sampler) and args.profile_range
+        if prof:
+            torch.cuda.profiler.start()
         # timed steps: no statistics read-back inside the timed region (it
         # synchronises after every step and is not part of the work)
         for i in range(steps):
@@ -694,6 +704,8 @@ def run_gpu(args):
             step(o)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
+        if prof:
+            torch.cuda.profiler.stop()
         clk = sampler.stop() if sampler else None
         step_ms = [a.elapsed_time(b) for a, b in ev]
         el = max_over_ranks(sum(step_ms), ws, "cuda")
@@ -840,6 +852,8 @@ def main():
     ap.add_argument("--all-forms", type=int, default=1, help="also time the other forms (plain, bound, chosen)")
     ap.add_argument("--train-queries", type=int, default=20000)
     ap.add_argument("--K", type=int, default=0, help="override the workload's K (e.g. 500 for the learned workload)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="wrap the headline form's timed steps in a CUDA profiler range")
     ap.add_argument("--form", default="chosen", choices=["plain", "bound", "chosen"],
                     help="plain: every hit scored; chosen: provable bound pruning (same output)")
     args = ap.parse_args()

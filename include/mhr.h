@@ -192,7 +192,11 @@ typedef struct {
  * Upload a graph and build its device indexes: the reverse CSR (in-edges of
  * each vertex, sorted by (source, relation)) and the norms behind the fp32
  * error bound.  Validates the description (MHR_EINVAL with a message on any
- * violation).  Synchronous; *out is NULL on failure.
+ * violation).  Synchronous; *out is NULL on failure, and a failed load has
+ * released every device allocation it made.  A service that must keep the
+ * graph within a memory budget sets the environment variable
+ * MHR_GRAPH_MEMORY_CAP_BYTES (decimal bytes, read at every load): a load
+ * whose resident device arrays would exceed it fails with MHR_ENOMEM.
  */
 mhr_status mhr_graph_load(const mhr_graph_desc* desc, mhr_graph** out, void* cuda_stream);
 

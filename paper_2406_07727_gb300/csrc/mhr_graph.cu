@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -367,13 +368,30 @@ struct Scoped {
 
 void free_graph(mhr_graph* g);
 
+// Device-memory cap of a resident graph (bytes), from MHR_GRAPH_MEMORY_CAP_BYTES;
+// 0 = none.  Read at every load.
+size_t graph_memory_cap() {
+    const char* v = std::getenv("MHR_GRAPH_MEMORY_CAP_BYTES");
+    if (!v || !*v) return 0;
+    char* end = nullptr;
+    const unsigned long long c = std::strtoull(v, &end, 10);
+    return (end && *end == '\0') ? static_cast<size_t>(c) : 0;
+}
+
 mhr_status graph_alloc(mhr_graph* g, void** p, size_t bytes) {
-    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    const size_t want = bytes ? bytes : 16;
+    if (g->memory_cap && g->alloc_bytes + want > g->memory_cap) {
+        *p = nullptr;
+        return fail(MHR_ENOMEM, "graph device memory would exceed MHR_GRAPH_MEMORY_CAP_BYTES (" +
+                                    std::to_string(g->memory_cap) + " bytes)");
+    }
+    cudaError_t e = cudaMalloc(p, want);
     if (e != cudaSuccess) {
         *p = nullptr;
         return cuda_fail(e, "cudaMalloc (graph)");
     }
     g->allocations.push_back(*p);
+    g->alloc_bytes += want;
     return MHR_OK;
 }
 
@@ -587,6 +605,7 @@ extern "C" mhr_status mhr_graph_load(const mhr_graph_desc* desc, mhr_graph** out
         delete g;
         return fail(MHR_ECUDA, "no CUDA device");
     }
+    g->memory_cap = graph_memory_cap();
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     mhr_status rc = load_impl(desc, g, st);
     if (rc != MHR_OK) {

@@ -73,6 +73,8 @@ struct mhr_graph {
     mhr_score_fn fn = MHR_SCORE_TRANSE_L1;
     // device storage
     std::vector<void*> allocations;
+    size_t alloc_bytes = 0;  // device bytes held in `allocations`
+    size_t memory_cap = 0;   // MHR_GRAPH_MEMORY_CAP_BYTES at load (0 = none)
     // host copies of the row starts (query sizing)
     std::vector<int64_t> h_off, h_roff;
     int64_t max_out_deg = 0, max_in_deg = 0;
