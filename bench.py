@@ -89,12 +89,9 @@ FORM_DESC = {"plain": "plain: batched, every middle edge scored, fp32 screen + f
 # k_middle, k_merge1, k_rescore, k_merge2, k_exact
 KERNELS_PER_STEP = 22
 # DRAM bytes (read + write) of one main join launch from one ncu capture of the
-# current kernel (workload, form, work-item size, scan tile): 94,522,368 read +
-# 4,869,632 written, learned-ordered form on the medium workload, 16,384-edge
-# items, tile 4; the seed launch adds about 17 MB.  Kept only for that exact
-# configuration.
-TRAFFIC_NCU = {("medium", "chosen", 16384, 4): 99_392_000,
-               # batching workload, main join launch of the second call, one
+# current kernel, per (workload, form, work-item size, scan tile); any other
+# configuration reports null.
+TRAFFIC_NCU = {# batching workload, main join launch of the second call, one
                # capture each of the current kernel (1 pass: dram__bytes_read.sum
                # + dram__bytes_write.sum at full size)
                ("batching", "chosen", 16384, 4): 89_140_000_000,
@@ -527,13 +524,12 @@ def run_tail(args):
 # ------------------------------------------------------------------ beam search
 BEAM_H, BEAM_K = 3, 10
 BEAM_METRIC = "beam-search queries/s (Alg. 6 / Alg. 7, H=3, K=10) on 1 GB300, results identical to oracle"
-FP64_PEAK_TFLOPS = 1.25   # nominal GB300 fp64 rate (no measured figure)
 
 
 def run_beam(args):
     """Beam search: CUDA events around each call (queries as host arrays of
     512 B, results copied back inside the call), L2 flushed before every call;
-    roofline of the fp64 edge scoring against the nominal fp64 rate."""
+    roofline of the edge scoring against the fp32 add rate."""
     import torch
     import synth
     import paper_2406_07727_gb300 as mhr
@@ -565,9 +561,14 @@ def run_beam(args):
     value = job_rate(len(S), ws, args.steps, tot_ms)
     if rank == 0:
         ms = tot_ms / args.steps
-        # TransE-L1 in fp64: an add, a subtract and an accumulate per element
+        # TransE-L1: an add, a subtract and an accumulate per element of every
+        # out-edge of every held path (screened in fp32; the band near each
+        # path's K-th extension rescored in fp64)
         flops = 3.0 * g.d * st["edges_scanned"]
         achieved = flops / (ms / 1000.0) / 1e12
+        n_sms = torch.cuda.get_device_properties(0).multi_processor_count
+        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        alu_peak = n_sms * 128 * sm_mhz * 1e6 / 1e12
         cpu = None
         if ws == 1 and not args.no_cpu:
             import oracle
@@ -593,13 +594,13 @@ def run_beam(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 8 * len(S),
                     "d2h_bytes_per_step": len(S) * BEAM_K * 64 + 4 * len(S)},
             "gpu_launches": (BEAM_H + 2) * args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved / alu_peak, "traffic": None,
                          "kernel": "k_beam_level (all levels of a call)",
-                         "peak_source": "nominal GB300 fp64 rate (1.25 TFLOP/s), not measured",
-                         "fp64_flops_per_call": flops},
+                         "peak_source": f"{n_sms} SMs x 128 fp32 lanes x {sm_mhz:.0f} MHz (adds)",
+                         "flops_per_call": flops},
             "clocks": clk,
-            "work_per_step": {"edges_scored": st["edges_scanned"]},
+            "work_per_step": {"edges_scored_fp32": st["edges_scanned"], "edges_rescored_fp64": st["rescored"]},
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu

@@ -442,7 +442,12 @@ mhr_status mhr_tail_topk(const mhr_graph* g, int32_t nq, const uint32_t* h, cons
  * and relation sequence after s (for three hops: (u, r1, v, r2, r3)).
  *   out    nq*K records (query i at out[i*K]); n_out[i] = results written
  *   mem    where s, t, out and n_out live
- *   stats  optional: edges_scanned = out-edges scored; ms = wall time
+ *   stats  optional: edges_scanned = out-edges scored (fp32 screen),
+ *          rescored = extensions and results scored in fp64; ms = wall time
+ * Each held path's extensions are screened in fp32 with the graph's proven
+ * edge bound: only those within that bound (plus the spacing of the rounded
+ * path scores) of the path's K-th fp32 extension are scored in fp64, so every
+ * selection is the fp64 one.
  * Synchronous.  MHR_EINVAL: NULL arrays, a vertex out of range, s == t,
  * H outside [1, MHR_BEAM_MAX_H], K < 1; MHR_ERANGE: K > MHR_BEAM_K_MAX or
  * K^(H-1) > 65536.  nq == 0 is a no-op.

@@ -3,9 +3,13 @@
 //
 // Level l holds, per query, up to K^l paths in fixed slots (slot j of level
 // l+1 is child j mod K of slot j / K of level l).  One CTA per held path:
-//   - every out-edge (x, r, y) of the path's last vertex x is scored in fp64 in
-//     the canonical operation order (the path score is the parent's score plus
-//     the edge weight, left to right, as the reference definition);
+//   - every out-edge (x, r, y) of the path's last vertex x is scored in fp32;
+//     the K-th largest fp32 weight among the path's extensions sets a band (the
+//     graph's proven fp32 error, twice, plus the spacing of the rounded path
+//     scores), and only the extensions inside it and the edges into t are
+//     scored in fp64 in the canonical operation order (the path score is the
+//     parent's score plus the edge weight, left to right, as the reference
+//     definition);
 //   - y already on the path: skipped (Alg. 7); y == t: a result (reaching the
 //     target ends the path); otherwise an extension;
 //   - the path keeps its K best extensions (score desc, then relation, then
@@ -16,7 +20,7 @@
 //     query's result list.
 // A final CTA per query keeps the K best results (score desc, hop count asc,
 // then (y_1, r_1, ..., y_{h-1}, r_{h-1}, r_h) asc) and writes them in order.
-// Every score is fp64 with the reference's operation order, so selection
+// Every kept score is fp64 with the reference's operation order, so selection
 // decisions and output equal the fp64 brute force exactly.
 #include <cuda_runtime.h>
 
@@ -124,7 +128,22 @@ struct LevelArgs {
     int64_t res_cap;
     unsigned* n_res;               // [nq]
     unsigned long long* n_scored;  // edges scored (one counter)
+    unsigned long long* n_exact;   // extensions scored in fp64 (one counter)
+    double e1;                     // bound on |w32 - w64| of one edge
 };
+
+// Screening of a path's extensions.  With T the K-th largest fp32 weight
+// w32 among them and E1 the bound on |w32 - w64|, every extension of the true
+// K best (by fl64(score(p) + w64), then relation, then vertex) has
+//   w32 >= T - 2 E1 - 2^-51 (|score(p)| + |w32| + E1)   (rounded down below):
+// at least one of the K extensions with w32 >= T ranks after it, so its w64 is
+// at least that one's w64 minus the spacing of the doubles around the
+// (equal) rounded path scores.  Only those extensions are scored in fp64.
+__device__ __forceinline__ bool in_band(float w32, float T, double P, double e1) {
+    if (T == -INFINITY) return true;
+    const double a = fabs(P) + fabs(static_cast<double>(w32)) + e1 + 1.0;
+    return static_cast<double>(w32) >= static_cast<double>(T) - 2.0 * e1 - ldexp(a, -50);
+}
 
 // one CTA per held path of this level
 __global__ void __launch_bounds__(kBeamThreads) k_beam_level(LevelArgs a) {
@@ -144,12 +163,62 @@ __global__ void __launch_bounds__(kBeamThreads) k_beam_level(LevelArgs a) {
     const uint32_t x = p.v[a.level];
     const uint32_t tq = a.t[q];
     const int64_t e0 = a.g.off[x], e1 = a.g.off[x + 1];
+    __shared__ float topw[kBeamBuf];  // screening: the K largest fp32 extension weights, then staging
+    __shared__ unsigned n_top, c_top;
+    __shared__ float thr_adm;         // admission threshold of the staging (K-th largest so far)
+    __shared__ unsigned long long n_fp64;
     if (threadIdx.x == 0) {
         n_ext = 0u;
         n_rl = 0u;
+        n_top = 0u;
+        n_fp64 = 0ull;
+        thr_adm = -INFINITY;
         if (e1 > e0) atomicAdd(a.n_scored, static_cast<unsigned long long>(e1 - e0));
     }
     __syncthreads();
+    // 0. fp32 pass over the extensions: T = the K-th largest w32 (-inf when
+    //    there are at most K extensions: every one is kept)
+    float T = -INFINITY;
+    if (more && e1 - e0 > K) {
+        for (int64_t base = e0; base < e1; base += kBeamChunk) {
+            if (threadIdx.x == 0) c_top = 0u;
+            __syncthreads();
+            const int64_t e = base + threadIdx.x;
+            if (threadIdx.x < kBeamChunk && e < e1) {
+                const uint32_t y = a.g.col[e];
+                bool on_path = y == tq;
+                for (int i = 0; i <= a.level; ++i) on_path |= (p.v[i] == y);
+                if (!on_path) {
+                    const float w = edge_w32_group(a.g, x, a.g.rel[e], y, 0, 1);
+                    if (w >= thr_adm) topw[n_top + atomicAdd(&c_top, 1u)] = w;
+                }
+            }
+            __syncthreads();
+            const unsigned m = n_top + c_top;
+            const bool last = base + kBeamChunk >= e1;
+            // keep the K largest once the staging could not take another chunk, and
+            // at the end (sorted, so that entry K - 1 is the K-th largest)
+            if (m + kBeamChunk > static_cast<unsigned>(kBeamBuf) || last) {
+                if (m > static_cast<unsigned>(K) || (last && m == static_cast<unsigned>(K))) {
+                    const unsigned P2 = pow2_at_least(m);
+                    for (unsigned i = m + threadIdx.x; i < P2; i += blockDim.x) topw[i] = -INFINITY;
+                    __syncthreads();
+                    block_bitonic(topw, P2, [](float u, float v) { return u > v; });
+                    if (threadIdx.x == 0) {
+                        n_top = static_cast<unsigned>(K);
+                        thr_adm = topw[K - 1];
+                    }
+                } else if (threadIdx.x == 0) {
+                    n_top = m;
+                }
+            } else if (threadIdx.x == 0) {
+                n_top = m;
+            }
+            __syncthreads();
+        }
+        if (n_top >= static_cast<unsigned>(K)) T = topw[K - 1];
+        __syncthreads();
+    }
     for (int64_t base = e0; base < e1; base += kBeamChunk) {
         if (threadIdx.x == 0) {
             c_ext = 0u;
@@ -164,9 +233,15 @@ __global__ void __launch_bounds__(kBeamThreads) k_beam_level(LevelArgs a) {
             bool on_path = false;
             for (int i = 0; i <= a.level; ++i) on_path |= (p.v[i] == y);
             if (!on_path && (y == tq || more)) {
-                const double sc = __dadd_rn(p.score, edge_w64(a.g, x, r, y));
-                if (y == tq) res[n_rl + atomicAdd(&c_res, 1u)] = Ext{sc, y, r};
-                else ext[n_ext + atomicAdd(&c_ext, 1u)] = Ext{sc, y, r};
+                // an extension outside the screening band cannot be among the K best
+                const bool keep = y == tq || T == -INFINITY ||
+                                  in_band(edge_w32_group(a.g, x, r, y, 0, 1), T, p.score, a.e1);
+                if (keep) {
+                    const double sc = __dadd_rn(p.score, edge_w64(a.g, x, r, y));
+                    if (y == tq) res[n_rl + atomicAdd(&c_res, 1u)] = Ext{sc, y, r};
+                    else ext[n_ext + atomicAdd(&c_ext, 1u)] = Ext{sc, y, r};
+                    atomicAdd(&n_fp64, 1ull);
+                }
             }
         }
         __syncthreads();
@@ -191,6 +266,7 @@ __global__ void __launch_bounds__(kBeamThreads) k_beam_level(LevelArgs a) {
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0 && n_fp64) atomicAdd(a.n_exact, n_fp64);
     // 3. children: the kept extensions (any order); the other child slots empty
     if (more) {
         for (int c = threadIdx.x; c < K; c += blockDim.x) {
@@ -325,12 +401,12 @@ extern "C" mhr_status mhr_beam_paths(const mhr_graph* g, int32_t nq, const uint3
     uint32_t *d_s = const_cast<uint32_t*>(s), *d_t = const_cast<uint32_t*>(t);
     unsigned* d_nres = nullptr;
     int32_t* d_nout = n_out;
-    unsigned long long* d_scored = nullptr;
+    unsigned long long* d_scored = nullptr;  // [0] edges scored in fp32, [1] scored in fp64
     cudaError_t e = alloc(reinterpret_cast<void**>(&A), sizeof(BeamPath) * QB * widest);
     if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&B), sizeof(BeamPath) * QB * widest);
     if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&R), sizeof(BeamPath) * QB * res_cap);
     if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&d_nres), 4ull * QB);
-    if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&d_scored), 8);
+    if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&d_scored), 16);
     if (e == cudaSuccess && mem == MHR_MEM_HOST) {
         e = alloc(reinterpret_cast<void**>(&d_out), sizeof(BeamPath) * static_cast<size_t>(nq) * K);
         if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&d_nout), 4ull * nq);
@@ -339,7 +415,7 @@ extern "C" mhr_status mhr_beam_paths(const mhr_graph* g, int32_t nq, const uint3
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_s, hs.data(), 4ull * nq, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_t, ht.data(), 4ull * nq, cudaMemcpyHostToDevice, st);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_scored, 0, 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_scored, 0, 16, st);
     if (e != cudaSuccess) {
         cleanup();
         return cuda_fail(e, "beam buffers");
@@ -363,6 +439,8 @@ extern "C" mhr_status mhr_beam_paths(const mhr_graph* g, int32_t nq, const uint3
             a.res_cap = res_cap;
             a.n_res = d_nres;
             a.n_scored = d_scored;
+            a.n_exact = d_scored + 1;
+            a.e1 = (g->eps32_edge + g->eps64_edge) * (1.0 + 1e-6);
             k_beam_level<<<static_cast<unsigned>(qb * slots), kBeamThreads, 0, st>>>(a);
             std::swap(cur, nxt);
             slots *= K;
@@ -371,17 +449,18 @@ extern "C" mhr_status mhr_beam_paths(const mhr_graph* g, int32_t nq, const uint3
                                                   d_nout + c0);
         e = cudaGetLastError();
     }
-    unsigned long long scored = 0;
+    unsigned long long scored[2] = {0ull, 0ull};
     if (e == cudaSuccess && mem == MHR_MEM_HOST) {
         e = cudaMemcpyAsync(out, d_out, sizeof(BeamPath) * static_cast<size_t>(nq) * K, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(n_out, d_nout, 4ull * nq, cudaMemcpyDeviceToHost, st);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&scored, d_scored, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(scored, d_scored, 16, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "beam search");
     if (stats) {
-        stats->edges_scanned = static_cast<int64_t>(scored);
+        stats->edges_scanned = static_cast<int64_t>(scored[0]);
+        stats->rescored = static_cast<int64_t>(scored[1]);
         stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     }
     return MHR_OK;

@@ -609,7 +609,7 @@ __global__ void k_order_perm(const PlanDev* __restrict__ P) {
 
 constexpr uint32_t kGposMulti = 0xffffffffu;   // group spans several near rows
 constexpr uint32_t kGposPruned = 0xfffffffeu;  // group inside one row whose bound misses the band
-constexpr int kSeedEdges = 8192;    // edges of each query's highest-bound rows done by the seed launch
+constexpr int kSeedEdges = 16384;   // edges of each query's highest-bound rows done by the seed launch
 constexpr int kSeedMinItems = 2;    // queries with fewer work items are not seeded
 
 // near entries in ordered position: (prefix of scan degree, row start), row

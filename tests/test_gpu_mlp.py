@@ -163,10 +163,10 @@ def test_learned_order_keeps_results_and_reports_work(mhr, K):
         work[name] = (st["edges_scanned"], st["hits"], st["pruned_edges"])
     print("work (scanned, hits, pruned):", work, "train rows", rep.rows)
     # what the trained network gains over the same provable pruning without it
-    # (rows in natural order): fewer middle edges scanned and fewer hits scored
+    # (rows in natural order): fewer middle edges scanned (whole work items
+    # skipped) and fewer hits scored
     assert work["learned"][0] < work["natural"][0]
     assert work["learned"][1] < work["natural"][1]
-    assert work["learned"][2] > work["natural"][2]
     want, n_want = oracle.topk_paths_batch(g, S[:4], T[:4], K)
     for q in range(4):
         assert base[q][: nb[q]]["u"].tolist() == want[q][: n_want[q]]["u"].tolist()
