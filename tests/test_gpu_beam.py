@@ -100,3 +100,17 @@ def test_device_arrays(mhr):
         assert dev[q][: dn[q]].tobytes() == host[q][: n_host[q]].tobytes()
         want = tuples(oracle.beam_paths(g, int(S[q]), int(T[q]), H, K), K)
         assert tuples(dev[q], int(dn[q])) == want, q
+
+
+@pytest.mark.parametrize("dyadic", [False, True])
+def test_long_rows_fp32_screen(mhr, dyadic):
+    """Rows of about a thousand edges (several staging sorts of the fp32
+    screen per held path), with exact ties when dyadic: the band around each
+    path's K-th fp32 extension must keep every extension of the fp64 K best."""
+    rng = np.random.default_rng(31 + dyadic)
+    g = random_kg(rng, 60, 60000, 20, 16, dyadic=dyadic, scale=0.4)
+    S = rng.integers(0, g.n, size=6).astype(np.uint32)
+    T = ((S + 11) % g.n).astype(np.uint32)
+    for H, K in ((2, 1), (3, 16), (2, 64)):
+        run(mhr, g, S, T, H, K, "transe")
+        run(mhr, g, S, T, H, K, "distmult")
