@@ -307,7 +307,10 @@ __global__ void k_edge_scores64(DevGraph g, const uint32_t* __restrict__ src,
 }
 
 // per-vertex maximum fp32 weight over out-edges and in-edges (order keys)
-__global__ void k_vertex_maxw(DevGraph g, int width, uint32_t* __restrict__ kout, uint32_t* __restrict__ kin) {
+// Per-vertex maxima of the fp32 weight of its out- and in-edges and, when the
+// tables are given, per (vertex, relation) maxima (kout_r[u * R + r]).
+__global__ void k_vertex_maxw(DevGraph g, int width, uint32_t* __restrict__ kout, uint32_t* __restrict__ kin,
+                              uint32_t* __restrict__ kout_r, uint32_t* __restrict__ kin_r) {
     const int lane = threadIdx.x & 31;
     const int sub = lane & (width - 1);
     const int64_t group = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / width;
@@ -327,6 +330,10 @@ __global__ void k_vertex_maxw(DevGraph g, int width, uint32_t* __restrict__ kout
             const uint32_t k = f2key(w);
             atomicMax(&kout[u], k);
             atomicMax(&kin[v], k);
+            if (kout_r) {
+                atomicMax(&kout_r[static_cast<int64_t>(u) * g.R + r], k);
+                atomicMax(&kin_r[static_cast<int64_t>(v) * g.R + r], k);
+            }
         }
     }
 }
@@ -537,20 +544,36 @@ mhr_status load_impl(const mhr_graph_desc* desc, mhr_graph* g, cudaStream_t st) 
             remb, desc->emb_dtype, cnt, g->wsplit, g->wsplit + cnt);
         MHR_CUDA_TRY(cudaGetLastError());
     }
-    // per-vertex bounds on the fp32 weight of adjacent edges (bound pruning)
+    // per-vertex bounds on the fp32 weight of adjacent edges (bound pruning),
+    // and per (vertex, relation) bounds when n x R entries stay within
+    // kMaxRelBoundEntries (4 bytes each, two tables)
     {
-        uint32_t *kout, *kin;
+        uint32_t *kout, *kin, *kout_r = nullptr, *kin_r = nullptr;
         MHR_TRY(graph_alloc(g, reinterpret_cast<void**>(&kout), sizeof(uint32_t) * n));
         MHR_TRY(graph_alloc(g, reinterpret_cast<void**>(&kin), sizeof(uint32_t) * n));
         MHR_CUDA_TRY(cudaMemsetAsync(kout, 0, sizeof(uint32_t) * n, st));
         MHR_CUDA_TRY(cudaMemsetAsync(kin, 0, sizeof(uint32_t) * n, st));
-        if (E) k_vertex_maxw<<<grid, 256, 0, st>>>(dg, score_group_width(d, desc->emb_dtype), kout, kin);
+        const int64_t nr = n * static_cast<int64_t>(R);
+        if (nr <= kMaxRelBoundEntries) {
+            MHR_TRY(graph_alloc(g, reinterpret_cast<void**>(&kout_r), sizeof(uint32_t) * nr));
+            MHR_TRY(graph_alloc(g, reinterpret_cast<void**>(&kin_r), sizeof(uint32_t) * nr));
+            MHR_CUDA_TRY(cudaMemsetAsync(kout_r, 0, sizeof(uint32_t) * nr, st));
+            MHR_CUDA_TRY(cudaMemsetAsync(kin_r, 0, sizeof(uint32_t) * nr, st));
+        }
+        if (E)
+            k_vertex_maxw<<<grid, 256, 0, st>>>(dg, score_group_width(d, desc->emb_dtype), kout, kin, kout_r, kin_r);
         k_maxw_finish<<<grid, 256, 0, st>>>(kout, n, 2.0 * g->eps32_edge);
         k_maxw_finish<<<grid, 256, 0, st>>>(kin, n, 2.0 * g->eps32_edge);
+        if (kout_r) {
+            k_maxw_finish<<<grid, 256, 0, st>>>(kout_r, nr, 2.0 * g->eps32_edge);
+            k_maxw_finish<<<grid, 256, 0, st>>>(kin_r, nr, 2.0 * g->eps32_edge);
+        }
         MHR_CUDA_TRY(cudaGetLastError());
         MHR_CUDA_TRY(cudaStreamSynchronize(st));
         dg.maxw_out = reinterpret_cast<const float*>(kout);
         dg.maxw_in = reinterpret_cast<const float*>(kin);
+        dg.maxw_out_r = reinterpret_cast<const float*>(kout_r);
+        dg.maxw_in_r = reinterpret_cast<const float*>(kin_r);
     }
     const double big = 1e30;
     if (!(g->max_l1 < big && g->max_rel_l1 < big && g->max_l2sq < big && g->max_rel_inf < big &&

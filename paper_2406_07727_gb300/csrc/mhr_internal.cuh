@@ -53,7 +53,13 @@ struct DevGraph {
     // weight over the out-edges / in-edges of each vertex; -inf if none
     const float* maxw_out;
     const float* maxw_in;
+    // the same per (vertex, relation): [n x R], entry v * R + r; NULL when
+    // n x R exceeds kMaxRelBoundEntries
+    const float* maxw_out_r;
+    const float* maxw_in_r;
 };
+
+constexpr int64_t kMaxRelBoundEntries = int64_t(1) << 29;  // 2 GiB per table
 
 // device allocation owned by the graph
 struct DevBuf {

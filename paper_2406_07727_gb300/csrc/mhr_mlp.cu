@@ -135,33 +135,127 @@ __global__ void __launch_bounds__(256) k_mlp_bwd_cols(const float* __restrict__ 
     }
 }
 
-// dW1[o][i] = sum_r dZ[r][o] X[r][i]; 64 x 64 output tile per block
-__global__ void __launch_bounds__(256) k_mlp_dw1(const float* __restrict__ dz, const uint16_t* __restrict__ X,
-                                                 int64_t n, float* __restrict__ grads) {
-    __shared__ float sz[32][65], sx[32][65];
-    const int o0 = blockIdx.y * 64, i0 = blockIdx.x * 64;
-    const int to = (threadIdx.x >> 4) * 4, ti = (threadIdx.x & 15) * 4;
-    float acc[4][4] = {};
-    for (int64_t rb = 0; rb < n; rb += 32) {
-        for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
-            const int rr = e >> 6, cc = e & 63;
-            const int64_t r = rb + rr;
-            sz[rr][cc] = r < n ? dz[r * kMlpHid + o0 + cc] : 0.f;
-            sx[rr][cc] = r < n ? __bfloat162float(__ushort_as_bfloat16(X[r * kMlpIn + i0 + cc])) : 0.f;
-        }
-        __syncthreads();
-        for (int rr = 0; rr < 32; ++rr) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] += sz[rr][to + a] * sx[rr][ti + b];
-        }
-        __syncthreads();
+// dW1 = dZ^T X on the tensor cores (tcgen05).  CTA (bx, by) owns hidden units
+// 128 by .. +127 and inputs 64 bx .. +63 (M = 128, N = 64, 64 TMEM columns) and
+// runs over all rows in chunks of 64 (the contraction dimension): dZ^T is
+// staged as bf16 hi + lo parts (dZ = hi + lo + r, |r| <= 2^-16 |dZ|; two MMAs
+// per K step), X^T as bf16 (exact); both are transposed into K-major core
+// matrices on the way into shared memory.  Each output element is summed by
+// one CTA in a fixed order, so gradients are deterministic.  A chunk whose MMA
+// does not complete within a second makes the CTA's gradients NaN.
+constexpr int kDwRows = 64;  // rows of dZ / X per chunk
+struct DwSmem {
+    alignas(128) uint8_t Ahi[kTcRows * kDwRows * 2];
+    alignas(128) uint8_t Alo[kTcRows * kDwRows * 2];
+    alignas(128) uint8_t B[64 * kDwRows * 2];
+    uint64_t bar;
+    uint32_t tmem;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_dw1_tc(const float* __restrict__ dz, const uint16_t* __restrict__ X,
+                                                              int64_t n, float* __restrict__ grads) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    DwSmem& sm = *reinterpret_cast<DwSmem*>(smem_raw);
+    const int i0 = blockIdx.x * 64, o0 = blockIdx.y * kTcRows;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) tc::tmem_alloc(&sm.tmem, 64);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&sm.bar, 1);
+        tc::mbar_fence_init();
     }
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int64_t r0 = 0; r0 < n && ok; r0 += kDwRows) {
+        // 128 core matrices of dZ^T (16 hidden blocks x 8 row blocks), 64 of X^T (8 x 8)
+        for (int job = threadIdx.x; job < 192; job += blockDim.x) {
+            if (job < 128) {
+                const int og = job >> 3, rg = job & 7;
+                float v[8][8];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+                for (int j = 0; j < 8; ++j) {
+                    const int64_t row = r0 + rg * 8 + j;
+                    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+                    if (row < n) {
+                        const float4* src = reinterpret_cast<const float4*>(dz + row * kMlpHid + o0 + og * 8);
+                        a = __ldg(src);
+                        b = __ldg(src + 1);
+                    }
+                    v[j][0] = a.x; v[j][1] = a.y; v[j][2] = a.z; v[j][3] = a.w;
+                    v[j][4] = b.x; v[j][5] = b.y; v[j][6] = b.z; v[j][7] = b.w;
+                }
 #pragma unroll
-        for (int b = 0; b < 4; ++b) grads[(o0 + to + a) * kMlpIn + i0 + ti + b] = acc[a][b];
+                for (int k = 0; k < 8; ++k) {
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const float x0 = v[2 * m][k], x1 = v[2 * m + 1][k];
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+                        hw[m] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) |
+                                (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+                        lw[m] = pack_bf16x2(x0 - __bfloat162float(h0), x1 - __bfloat162float(h1));
+                    }
+                    const uint32_t off = tc::core_offset(og * 8 + k, rg * 8, kDwRows);
+                    *reinterpret_cast<uint4*>(sm.Ahi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4*>(sm.Alo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+            } else {
+                const int b = job - 128, ig = b >> 3, rg = b & 7;
+                uint32_t w[8][4];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int64_t row = r0 + rg * 8 + j;
+                    uint4 t = make_uint4(0u, 0u, 0u, 0u);
+                    if (row < n) t = __ldg(reinterpret_cast<const uint4*>(X + row * kMlpIn + i0 + ig * 8));
+                    w[j][0] = t.x; w[j][1] = t.y; w[j][2] = t.z; w[j][3] = t.w;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const unsigned sel = (k & 1) ? 0x7632u : 0x5410u;  // high or low halves
+                    uint32_t o[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) o[m] = __byte_perm(w[2 * m][k >> 1], w[2 * m + 1][k >> 1], sel);
+                    *reinterpret_cast<uint4*>(sm.B + tc::core_offset(ig * 8 + k, rg * 8, kDwRows)) =
+                        make_uint4(o[0], o[1], o[2], o[3]);
+                }
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (threadIdx.x == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcRows, 64);
+            constexpr uint32_t sbo = (kDwRows / 8) * 128;
+            const uint32_t ah = tc::smem_u32(sm.Ahi), al = tc::smem_u32(sm.Alo), bb = tc::smem_u32(sm.B);
+#pragma unroll
+            for (int kk = 0; kk < kDwRows / 16; ++kk) {
+                const uint64_t bd = tc::smem_desc(bb + kk * 256, 128, sbo);
+                tc::mma_bf16(sm.tmem, tc::smem_desc(ah + kk * 256, 128, sbo), bd, idesc, (r0 > 0 || kk > 0) ? 1u : 0u);
+                tc::mma_bf16(sm.tmem, tc::smem_desc(al + kk * 256, 128, sbo), bd, idesc, 1u);
+            }
+            tc::mma_commit(&sm.bar);
+        }
+        const bool done = tc::mbar_wait(&sm.bar, phase, kTcWaitNs);
+        phase ^= 1u;
+        tc::fence_after_sync();
+        ok = !__syncthreads_or(done ? 0 : 1);
+    }
+    if (warp < 4) {
+        const int o = o0 + warp * 32 + lane;
+        float* dst = grads + static_cast<int64_t>(o) * kMlpIn + i0;
+        for (int c0 = 0; c0 < 64; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(sm.tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c0), v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) dst[c0 + i] = ok ? v[i] : __int_as_float(0x7fc00000);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(sm.tmem, 64);
+    }
 }
 
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m1,
@@ -235,7 +329,9 @@ extern "C" mhr_status mhr_mlp_backward(const mhr_mlp* m, const uint16_t* X, int6
     const int sms = std::max(1, device_sm_count());
     k_mlp_bwd_rows<<<sms * 4, 256, 0, st>>>(m->w2, y, target, z1, n, work);
     k_mlp_bwd_cols<<<kMlpHid / 32, 256, 0, st>>>(y, target, z1, work, n, grads, loss);
-    k_mlp_dw1<<<dim3(kMlpIn / 64, kMlpHid / 64), 256, 0, st>>>(work, X, n, grads);
+    MHR_CUDA_TRY(cudaFuncSetAttribute(k_mlp_dw1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(sizeof(DwSmem))));
+    k_mlp_dw1_tc<<<dim3(kMlpIn / 64, kMlpHid / kTcRows), kTcThreads, sizeof(DwSmem), st>>>(work, X, n, grads);
     MHR_CUDA_TRY(cudaGetLastError());
     return MHR_OK;
 }

@@ -1672,11 +1672,19 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                             }
                             n_paths_w += hal * hcl;
                             if (prune && alive) {
-                                // w2 <= the largest weight of any out-edge of u and of any in-edge of v
+                                // w2 <= the largest weight of any out-edge of u and of any in-edge of v,
+                                // and of those of relation r2 when the graph keeps that table
                                 const float mw2 = fminf(ea.midw, ec.midw);
                                 if (__fadd_ru(__fadd_rn(__fadd_rn(mw1, mw2), mw3), slack) < thr) {
                                     alive = false;
                                     ++n_pruned;
+                                } else if (g.maxw_out_r) {
+                                    const float mr = fminf(g.maxw_out_r[static_cast<int64_t>(hu) * g.R + hr2],
+                                                           g.maxw_in_r[static_cast<int64_t>(hv) * g.R + hr2]);
+                                    if (__fadd_ru(__fadd_rn(__fadd_rn(mw1, mr), mw3), slack) < thr) {
+                                        alive = false;
+                                        ++n_pruned;
+                                    }
                                 }
                             }
                         }
