@@ -832,6 +832,14 @@ def run_gpu(args):
             result["cpu_baseline"] = cpu
             result["oracle_parity"] = parity
         result["precision_error"] = perr
+        # the forms side by side (all return identical results)
+        rates = {args.form: value}
+        rates.update({k: v["value"] for k, v in others.items()})
+        result["form_comparison"] = {
+            "queries_per_s": rates,
+            "fastest": max(rates, key=rates.get),
+            "headline_vs_plain": (value / rates["plain"]) if "plain" in rates and args.form != "plain" else None,
+            "headline_vs_bound": (value / rates["bound"]) if "bound" in rates and args.form != "bound" else None}
         print(json.dumps(result), flush=True)
     G.close()
     if ws > 1:

@@ -45,8 +45,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(MlpDev m, cons
         float* zr = (z1 != nullptr && row < n) ? z1 + row * kMlpHid : nullptr;
         const float p = tc_row_half(
             sm.tmem, m.w2, [&](int c) { return __ldg(m.b1 + c); },
-            [&](int c, float z) {
-                if (zr) zr[c] = z;
+            [&](int c0, const float(&z)[32]) {
+                if (zr) {
+                    float4* d4 = reinterpret_cast<float4*>(zr + c0);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) d4[i] = make_float4(z[4 * i], z[4 * i + 1], z[4 * i + 2], z[4 * i + 3]);
+                }
             });
         sm.part[r][h] = p;
         __syncthreads();

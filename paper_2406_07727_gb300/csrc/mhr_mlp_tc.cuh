@@ -80,8 +80,9 @@ __device__ __forceinline__ bool tc_mma_tile(MlpTcSmem<KC>& sm, uint32_t& phase) 
 }
 
 // Epilogue for this thread's row (r = 32 (warp % 4) + lane) and half of the
-// hidden units; bias(c) and store_z(c, z) act on that row.  Returns the
-// partial output sum; the caller adds the halves (part) and b2.
+// hidden units; bias(c) acts on that row, store_z(c0, z) receives the row's
+// pre-activations of hidden units c0 .. c0 + 31.  Returns the partial output
+// sum; the caller adds the halves (part) and b2.
 template <typename Bias, typename StoreZ>
 __device__ __forceinline__ float tc_row_half(uint32_t tmem, const float* __restrict__ w2, Bias bias, StoreZ store_z) {
     const int warp = threadIdx.x >> 5;
@@ -94,10 +95,10 @@ __device__ __forceinline__ float tc_row_half(uint32_t tmem, const float* __restr
         tc::tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-            const float z = v[i] + bias(c0 + i);
-            store_z(c0 + i, z);
-            p += fmaxf(z, 0.f) * __ldg(w2 + c0 + i);
+            v[i] += bias(c0 + i);
+            p += fmaxf(v[i], 0.f) * __ldg(w2 + c0 + i);
         }
+        store_z(c0, v);
     }
     return p;
 }
