@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_keys(const PlanDev* __res
         const int h = threadIdx.x >> 7;
         const float* qb = P->mlp_qbias + static_cast<int64_t>(qrow[r]) * kMlpHid;
         const float p = tc_row_half(
-            sm.tmem, P->mlp.w2, [&](int c) { return qb[c]; }, [&](int, float) {});
+            sm.tmem, P->mlp.w2, [&](int c) { return qb[c]; }, [&](int, const float(&)[32]) {});
         sm.part[r][h] = p;
         __syncthreads();
         if (threadIdx.x < kTcRows && slot[threadIdx.x] >= 0) {
