@@ -679,6 +679,7 @@ def run_gpu(args):
 
     dense_steps = []
     spreads = []
+    expand_ms = []
 
     def timed(o, steps, sampler=None):
         for _ in range(args.warmup):
@@ -687,6 +688,7 @@ def run_gpu(args):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
         join_ms, dev_ms, st = [], [], None
+        exp_ms = []
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -718,8 +720,10 @@ def run_gpu(args):
             _, _, st = step(o, with_stats=True)
             join_ms.append(st["ms_join"])
             dev_ms.append(st["ms_device"])
+            exp_ms.append(st["ms_expand"])
             dense_steps.append(st["dense_queries"])
         spreads.append(step_ms)
+        expand_ms.append(statistics.mean(exp_ms))
         return el, join_ms, dev_ms, st, clk
 
     clocks = ClockSampler(local)
@@ -832,6 +836,17 @@ def run_gpu(args):
             result["cpu_baseline"] = cpu
             result["oracle_parity"] = parity
         result["precision_error"] = perr
+        # hop-1 / hop-3 expansion (a2, a3): CSR entries of the rows of s and t
+        # plus one embedding row per distinct frontier vertex, per launch
+        slots = sum(f["deg_s"] + f["deg_t"] for f in fs)
+        x_bytes = slots * (4 + 2) + eb * g.d * (n_vert + 2 * nq)
+        x_ms = expand_ms[0]
+        result["expansion_roofline"] = {
+            "bound": "hbm", "kernel": "k_expand (hop-1 / hop-3 expansion)",
+            "achieved": x_bytes / (x_ms / 1000.0) / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": x_bytes / (x_ms / 1000.0) / 1e9 / peak, "alg_bytes_per_launch": x_bytes,
+            "bytes_loaded_per_launch": slots * (4 + 2 + eb * g.d), "avg_launch_ms": x_ms,
+            "peak_source": f"{peak_src} hbm_gbs"}
         # the forms side by side (all return identical results)
         rates = {args.form: value}
         rates.update({k: v["value"] for k, v in others.items()})

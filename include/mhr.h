@@ -186,6 +186,8 @@ typedef struct {
     double ms;             /* wall time of the call (synchronous calls only) */
     double ms_device;      /* device time of the whole launch sequence (CUDA events) */
     double ms_join;        /* device time of the middle-join kernel (CUDA events) */
+    double ms_expand;      /* device time of the hop-1 / hop-3 expansion kernel (CUDA events;
+                              batched three-hop search only) */
 } mhr_stats;
 
 /*

@@ -80,7 +80,7 @@ class Stats(ctypes.Structure):
                 ("paths", ctypes.c_int64), ("candidates", ctypes.c_int64), ("rescored", ctypes.c_int64),
                 ("pruned_edges", ctypes.c_int64), ("dense_queries", ctypes.c_int64),
                 ("ms", ctypes.c_double), ("ms_device", ctypes.c_double),
-                ("ms_join", ctypes.c_double)]
+                ("ms_join", ctypes.c_double), ("ms_expand", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

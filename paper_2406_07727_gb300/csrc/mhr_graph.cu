@@ -23,7 +23,7 @@ static_assert(sizeof(mhr_query_opts) == 48, "mhr_query_opts layout");
 static_assert(sizeof(mhr_constraints) == 40, "mhr_constraints layout");
 static_assert(sizeof(mhr_graph_info) == 80, "mhr_graph_info layout");
 static_assert(sizeof(mhr_mlp) == 32, "mhr_mlp layout");
-static_assert(sizeof(mhr_stats) == 80, "mhr_stats layout");
+static_assert(sizeof(mhr_stats) == 88, "mhr_stats layout");
 
 namespace mhr {
 

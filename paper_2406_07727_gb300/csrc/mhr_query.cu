@@ -195,6 +195,101 @@ __global__ void k_init(const PlanDev* __restrict__ P, DevGraph g) {
     for (int64_t i = tid; i < P->item_cap; i += stride) P->item_ub[i] = 0u;
 }
 
+// One expansion slot: its query, position in the row of s (hop-1 side) or the
+// reverse row of t (hop-3 side), the edge's far endpoint vtx and relation, the
+// previous entry's vertex (run heads) and vtx's scan degree.
+struct SlotInfo {
+    uint32_t s, t, vtx, r, prev, sdeg;
+    int64_t k;
+    int q;
+    bool sideA;
+};
+
+__device__ __forceinline__ SlotInfo slot_info(const PlanDev* __restrict__ P, const DevGraph& g, int64_t x, bool live) {
+    SlotInfo o;
+    o.s = o.t = o.vtx = o.r = o.sdeg = 0;
+    o.prev = 0xffffffffu;
+    o.k = 0;
+    o.q = 0;
+    o.sideA = true;
+    if (!live) return o;
+    const int64_t totA = P->totA;
+    o.sideA = x < totA;
+    const int64_t lx = o.sideA ? x : x - totA;
+    const int64_t* offs = o.sideA ? P->a_off : P->c_off;
+    o.q = static_cast<int>(upper_bound_i64(offs, P->nq + 1, lx) - 1);
+    o.k = lx - offs[o.q];
+    o.s = P->S[o.q];
+    o.t = P->T[o.q];
+    if (o.sideA) {
+        const int64_t p = g.off[o.s] + o.k;
+        o.vtx = g.col[p];
+        o.r = g.rel[p];
+        if (o.k > 0) o.prev = g.col[p - 1];
+        o.sdeg = static_cast<uint32_t>(g.off[o.vtx + 1] - g.off[o.vtx]);
+    } else {
+        const int64_t p = g.roff[o.t] + o.k;
+        o.vtx = g.rcol[p];
+        o.r = g.rrel[p];
+        if (o.k > 0) o.prev = g.rcol[p - 1];
+        o.sdeg = static_cast<uint32_t>(g.roff[o.vtx + 1] - g.roff[o.vtx]);
+    }
+    return o;
+}
+
+// Writes a slot's fp32 weight, exclusion and run-head flag and adds the
+// distinct frontier vertices' scan degrees to S_f / S_b.  All lanes call.
+__device__ __forceinline__ void slot_commit(const PlanDev* __restrict__ P, const DevGraph& g, int64_t x, bool live,
+                                            const SlotInfo& o, float wmine, int lane) {
+    uint32_t key = 0xffffffffu;
+    unsigned long long dsum = 0ull;
+    if (live) {
+        const uint32_t s = o.s, t = o.t, vtx = o.vtx, r = o.r;
+        const bool sideA = o.sideA;
+        const bool excl = (vtx == s) || (vtx == t);
+        // A vertex with no scan edges can neither be scanned nor be hit, so it
+        // never lies on a path: it is dropped from the distinct list.
+        bool head = !excl && o.sdeg > 0 && (o.k == 0 || o.prev != vtx);
+        // vertex partition: this call owns the paths whose hop-1 vertex u it owns
+        if (sideA && P->part_count > 1 && vtx % static_cast<uint32_t>(P->part_count) !=
+                                              static_cast<uint32_t>(P->part_index))
+            head = false;
+        bool allowed = true;
+        const uint8_t* cons = P->cons;
+        if (cons) {
+            // constrained query: a slot of a disallowed hop-1 / hop-3 relation
+            // weighs -inf; a vertex heads its run only when its type is allowed
+            // and at least one edge of the run has an allowed relation
+            const int R = g.R;
+            const uint8_t* rf = cons + (sideA ? 0 : 2 * R);
+            allowed = rf[r] != 0;
+            if (head) {
+                head = cons[3 * R + (sideA ? 0 : 256) + g.vtypes[vtx]] != 0;
+                if (head && !allowed) {
+                    const int64_t p0 = sideA ? g.off[s] : g.roff[t];
+                    const int64_t rlen = (sideA ? g.off[s + 1] : g.roff[t + 1]) - p0;
+                    const uint32_t* cc = sideA ? g.col : g.rcol;
+                    const uint16_t* rr = sideA ? g.rel : g.rrel;
+                    bool any = false;
+                    for (int64_t j = o.k + 1; j < rlen && cc[p0 + j] == vtx && !any; ++j) any = rf[rr[p0 + j]] != 0;
+                    head = any;
+                }
+            }
+        }
+        P->w32[x] = (excl || !allowed) ? neg_inf() : wmine;
+        P->flag[x] = head ? 1u : 0u;
+        P->w64own[x] = 0;
+        key = 2u * static_cast<uint32_t>(o.q) + (sideA ? 0u : 1u);
+        dsum = head ? o.sdeg : 0u;
+    }
+    // S_f / S_b: scan degrees of the distinct frontier vertices, summed per
+    // (query, side) with one atomic per run of lanes sharing the key
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    unsigned long long tot = 0ull;
+    for (unsigned m = peers; m; m &= m - 1) tot += __shfl_sync(peers, dsum, __ffs(m) - 1);
+    if (key != 0xffffffffu && lane == __ffs(peers) - 1 && tot) atomicAdd(&P->sdeg_q[key], tot);
+}
+
 // fp32 weight, exclusion and run-head flag of every slot.  Each lane resolves
 // one slot of its warp's 32 (query, CSR position, endpoint degree) in
 // parallel; then groups of G lanes score the 32 edges, H = 32 / G at a time.
@@ -202,8 +297,7 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, D
     const int lane = threadIdx.x & 31;
     const int G = P->score_width, H = 32 / G;
     const int sub = lane & (G - 1);
-    const int64_t X = P->X, totA = P->totA;
-    const int nq = P->nq;
+    const int64_t X = P->X;
     const int64_t warp_id = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
     // rows of at most two 16-byte vectors per lane: unrolled scorer
@@ -212,89 +306,20 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, D
     for (int64_t base = warp_id * 32; base < X; base += nwarps * 32) {  // warp-uniform
         const int64_t x = base + lane;
         const bool live = x < X;
-        uint32_t s = 0, t = 0, vtx = 0, r = 0, prev = 0xffffffffu, sdeg = 0;
-        int64_t k = 0;
-        bool sideA = true;
-        int q = 0;
-        if (live) {
-            sideA = x < totA;
-            const int64_t lx = sideA ? x : x - totA;
-            const int64_t* offs = sideA ? P->a_off : P->c_off;
-            q = static_cast<int>(upper_bound_i64(offs, nq + 1, lx) - 1);
-            k = lx - offs[q];
-            s = P->S[q];
-            t = P->T[q];
-            if (sideA) {
-                const int64_t p = g.off[s] + k;
-                vtx = g.col[p];
-                r = g.rel[p];
-                if (k > 0) prev = g.col[p - 1];
-                sdeg = static_cast<uint32_t>(g.off[vtx + 1] - g.off[vtx]);
-            } else {
-                const int64_t p = g.roff[t] + k;
-                vtx = g.rcol[p];
-                r = g.rrel[p];
-                if (k > 0) prev = g.rcol[p - 1];
-                sdeg = static_cast<uint32_t>(g.roff[vtx + 1] - g.roff[vtx]);
-            }
-        }
-        const uint32_t hu = sideA ? s : vtx, tv = sideA ? vtx : t;
+        const SlotInfo o = slot_info(P, g, x, live);
+        const uint32_t hu = o.sideA ? o.s : o.vtx, tv = o.sideA ? o.vtx : o.t;
         float wmine = 0.f;
         for (int rd = 0; rd < G; ++rd) {
             const int src = rd * H + lane / G;
             const uint32_t a = __shfl_sync(0xffffffffu, hu, src);
-            const uint32_t rr = __shfl_sync(0xffffffffu, r, src);
+            const uint32_t rr = __shfl_sync(0xffffffffu, o.r, src);
             const uint32_t b = __shfl_sync(0xffffffffu, tv, src);
             // dead lanes score vertex 0's rows
             const float w = vec2 ? edge_w32_group2(g, a, rr, b, sub, G) : edge_w32_group(g, a, rr, b, sub, G);
             const float tw = __shfl_sync(0xffffffffu, w, ((lane - rd * H) & (H - 1)) * G);
             if (lane / H == rd) wmine = tw;
         }
-        uint32_t key = 0xffffffffu;
-        unsigned long long dsum = 0ull;
-        if (live) {
-            const bool excl = (vtx == s) || (vtx == t);
-            // A vertex with no scan edges can neither be scanned nor be hit, so it
-            // never lies on a path: it is dropped from the distinct list.
-            bool head = !excl && sdeg > 0 && (k == 0 || prev != vtx);
-            // vertex partition: this call owns the paths whose hop-1 vertex u it owns
-            if (sideA && P->part_count > 1 && vtx % static_cast<uint32_t>(P->part_count) !=
-                                                  static_cast<uint32_t>(P->part_index))
-                head = false;
-            bool allowed = true;
-            const uint8_t* cons = P->cons;
-            if (cons) {
-                // constrained query: a slot of a disallowed hop-1 / hop-3 relation
-                // weighs -inf; a vertex heads its run only when its type is allowed
-                // and at least one edge of the run has an allowed relation
-                const int R = g.R;
-                const uint8_t* rf = cons + (sideA ? 0 : 2 * R);
-                allowed = rf[r] != 0;
-                if (head) {
-                    head = cons[3 * R + (sideA ? 0 : 256) + g.vtypes[vtx]] != 0;
-                    if (head && !allowed) {
-                        const int64_t p0 = sideA ? g.off[s] : g.roff[t];
-                        const int64_t rlen = (sideA ? g.off[s + 1] : g.roff[t + 1]) - p0;
-                        const uint32_t* cc = sideA ? g.col : g.rcol;
-                        const uint16_t* rr = sideA ? g.rel : g.rrel;
-                        bool any = false;
-                        for (int64_t j = k + 1; j < rlen && cc[p0 + j] == vtx && !any; ++j) any = rf[rr[p0 + j]] != 0;
-                        head = any;
-                    }
-                }
-            }
-            P->w32[x] = (excl || !allowed) ? neg_inf() : wmine;
-            P->flag[x] = head ? 1u : 0u;
-            P->w64own[x] = 0;
-            key = 2u * static_cast<uint32_t>(q) + (sideA ? 0u : 1u);
-            dsum = head ? sdeg : 0u;
-        }
-        // S_f / S_b: scan degrees of the distinct frontier vertices, summed per
-        // (query, side) with one atomic per run of lanes sharing the key
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        unsigned long long tot = 0ull;
-        for (unsigned m = peers; m; m &= m - 1) tot += __shfl_sync(peers, dsum, __ffs(m) - 1);
-        if (key != 0xffffffffu && lane == __ffs(peers) - 1 && tot) atomicAdd(&P->sdeg_q[key], tot);
+        slot_commit(P, g, x, live, o, wmine, lane);
     }
 }
 
@@ -2350,6 +2375,7 @@ struct Plan {
     cudaStream_t cap = nullptr;
     cudaEvent_t h2d_done = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // before / join / after / end
+    cudaEvent_t ev_x[2] = {nullptr, nullptr};  // around the expansion kernel (recorded inside the first graph)
     bool h2d_pending = false;
     void drop_graphs() {
         for (cudaGraphExec_t& x : exec)
@@ -2363,6 +2389,8 @@ struct Plan {
         if (cap) cudaStreamDestroy(cap);
         if (h2d_done) cudaEventDestroy(h2d_done);
         for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_x)
             if (e) cudaEventDestroy(e);
         for (void* p : fixed) cudaFree(p);
         if (slot_mem) cudaFree(slot_mem);
@@ -2534,7 +2562,11 @@ static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int
     const int64_t* nX = reinterpret_cast<const int64_t*>(p->dregion + offsetof(PlanDev, X));
     if (part == 0) {
         k_init<<<sms * 2, 256, 0, st>>>(d, g);
+        cudaError_t ee = cudaEventRecordWithFlags(p->ev_x[0], st, cudaEventRecordExternal);
+        if (ee != cudaSuccess) return ee;
         k_expand<<<sms * p->expand_per_sm, 256, 0, st>>>(d, g);
+        ee = cudaEventRecordWithFlags(p->ev_x[1], st, cudaEventRecordExternal);
+        if (ee != cudaSuccess) return ee;
         cudaError_t e = device_excl_scan<uint32_t>(p->h.flag, nX, p->h.partials, p->h.scan1, st);
         if (e != cudaSuccess) return e;
         k_lists<<<sms * 4, 256, 0, st>>>(d, g);
@@ -2705,6 +2737,10 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precisio
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
     e = cudaEventCreateWithFlags(&p->h2d_done, cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+    for (cudaEvent_t& ev : p->ev_x) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+    }
     for (cudaEvent_t& ev : p->ev) {
         e = cudaEventCreate(&ev);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
@@ -2878,6 +2914,9 @@ static mhr_status read_stats(Plan* p, cudaStream_t st, mhr_stats* stats) {
     if (cudaEventElapsedTime(&a, p->ev[0], p->ev[3]) != cudaSuccess) a = -1.f;
     // ev[1] .. ev[2] bracket the join graph
     if (cudaEventElapsedTime(&b, p->ev[1], p->ev[2]) != cudaSuccess) b = -1.f;
+    float x = -1.f;
+    if (cudaEventElapsedTime(&x, p->ev_x[0], p->ev_x[1]) != cudaSuccess) x = -1.f;
+    stats->ms_expand = x;
     cudaGetLastError();
     stats->ms_device = a;
     stats->ms_join = b;

@@ -46,7 +46,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(_mhr.QueryOpts) == 48
     assert ctypes.sizeof(_mhr.Constraints) == 40
     assert ctypes.sizeof(_mhr.GraphInfo) == 80
-    assert ctypes.sizeof(_mhr.Stats) == 80
+    assert ctypes.sizeof(_mhr.Stats) == 88
 
 
 def test_host_side_argument_checks():
