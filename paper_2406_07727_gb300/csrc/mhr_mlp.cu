@@ -2,6 +2,8 @@
 // gathering, and their C ABI.  The network orders intermediate vertices so
 // the K-th-score threshold of a query tightens early; it never decides what is
 // pruned (that is left to provable bounds), so it cannot change any result.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include "mhr_internal.cuh"
@@ -14,25 +16,49 @@ constexpr int kMlpParams = kMlpHid * kMlpIn + kMlpHid + kMlpHid + 1;  // W1, b1,
 
 // Dense forward on the tensor cores (tcgen05, accumulator in TMEM): one CTA
 // per SM runs 128-row tiles of X; y, and z1 (pre-activations) when asked.
-// A tile whose MMA does not complete within a second gets NaN outputs.
+// With a tensor map (tmap_ok), each whole tile is staged by one TMA load: a
+// 4-D view of X (8 columns, 8 rows, 32 column blocks, row groups) whose box
+// {8, 8, 32, 16} lands in shared memory exactly in the K-major core-matrix
+// layout the MMA descriptors describe; the ragged last tile, and every tile
+// without a map, is staged by the threads.  A tile whose TMA or MMA does not
+// complete within a second gets NaN outputs.
 __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(MlpDev m, const uint16_t* __restrict__ X,
                                                                   int64_t n, float* __restrict__ y,
-                                                                  float* __restrict__ z1) {
+                                                                  float* __restrict__ z1,
+                                                                  const __grid_constant__ CUtensorMap tmap,
+                                                                  int tmap_ok) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MlpTcSmem<kMlpIn>& sm = *reinterpret_cast<MlpTcSmem<kMlpIn>*>(smem_raw);
     tc_setup(sm);
     tc_stage_w1(sm, m.W1);
     const int64_t ntiles = (n + kTcRows - 1) / kTcRows;
-    uint32_t phase = 0;
+    const int64_t tma_tiles = tmap_ok && (tc::smem_u32(sm.A) & 127u) == 0u ? (n / 8) / 16 : 0;  // whole tiles
+    uint32_t phase = 0, tphase = 0;
     const uint4* Xv = reinterpret_cast<const uint4*>(X);
     const float b2 = __ldg(m.b2);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t r0 = tile * kTcRows;
-        for (int i = threadIdx.x; i < kTcRows * (kMlpIn / 8); i += blockDim.x) {
-            const int r = i >> 5, c = i & 31;
-            const int64_t row = r0 + r;
-            const uint4 v = row < n ? __ldg(Xv + row * (kMlpIn / 8) + c) : make_uint4(0u, 0u, 0u, 0u);
-            *reinterpret_cast<uint4*>(sm.A + tc::core_offset(r, c * 8, kMlpIn)) = v;
+        bool staged = true;
+        if (tile < tma_tiles) {
+            __syncthreads();  // the set-up (barrier init) and the previous tile's reads are done
+            if (threadIdx.x == 0) {
+                tc::mbar_arrive_expect_tx(&sm.tma_bar, kTcRows * kMlpIn * 2);
+                tc::tma_load_4d(sm.A, &tmap, 0, 0, 0, static_cast<int>(tile * (kTcRows / 8)), &sm.tma_bar);
+            }
+            staged = tc::mbar_wait(&sm.tma_bar, tphase, kTcWaitNs);
+            tphase ^= 1u;
+        } else {
+            for (int i = threadIdx.x; i < kTcRows * (kMlpIn / 8); i += blockDim.x) {
+                const int r = i >> 5, c = i & 31;
+                const int64_t row = r0 + r;
+                const uint4 v = row < n ? __ldg(Xv + row * (kMlpIn / 8) + c) : make_uint4(0u, 0u, 0u, 0u);
+                *reinterpret_cast<uint4*>(sm.A + tc::core_offset(r, c * 8, kMlpIn)) = v;
+            }
+        }
+        if (__syncthreads_or(staged ? 0 : 1)) {
+            const int64_t row = r0 + threadIdx.x;
+            if (threadIdx.x < kTcRows && row < n) y[row] = __int_as_float(0x7fc00000);
+            break;
         }
         const bool ok = tc_mma_tile(sm, phase);
         const int r = ((threadIdx.x >> 5) & 3) * 32 + (threadIdx.x & 31);
@@ -282,6 +308,37 @@ __global__ void k_to_bf16(const float* __restrict__ src, uint16_t* __restrict__ 
         dst[i] = __bfloat16_as_ushort(__float2bfloat16_rn(src[i]));
 }
 
+// Tensor map of the feature matrix X [n x 256] bf16 viewed as 4-D: element
+// (e, i, c, g) = X[8 g + i][8 c + e], strides 2 B (implicit), 512 B, 16 B,
+// 4096 B; a box of {8, 8, 32, 16} is one 128-row tile in the K-major
+// core-matrix layout.  Whole groups of 8 rows only (the kernel stages a
+// ragged tail itself).  The driver's encoder is looked up once through the
+// runtime; false (threads stage every tile) when it is missing, when X is
+// not 16-byte aligned or when the encoder declines the view.
+static bool encode_feature_map(const uint16_t* X, int64_t n, CUtensorMap* out) {
+    static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        cudaGetLastError();
+    }
+    const int64_t groups = n / 8;
+    if (!enc || groups < 16 || (reinterpret_cast<uintptr_t>(X) & 15u)) return false;
+    const cuuint64_t dims[4] = {8, 8, kMlpIn / 8, static_cast<cuuint64_t>(groups)};
+    const cuuint64_t strides[3] = {kMlpIn * 2, 16, 8 * kMlpIn * 2};
+    const cuuint32_t box[4] = {8, 8, kMlpIn / 8, kTcRows / 8};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t*>(X), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 static MlpDev to_dev(const mhr_mlp* m) {
     MlpDev d;
     d.W1 = m->W1;
@@ -319,7 +376,10 @@ extern "C" mhr_status mhr_mlp_forward(const mhr_mlp* m, const uint16_t* X, int64
     const int grid = static_cast<int>(std::min<int64_t>(tiles, std::max(1, device_sm_count())));
     const int sb = static_cast<int>(sizeof(MlpTcSmem<kMlpIn>));
     MHR_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sb));
-    k_mlp_forward_tc<<<grid, kTcThreads, sb, static_cast<cudaStream_t>(cuda_stream)>>>(to_dev(m), X, n, y, z1);
+    CUtensorMap tmap;
+    const int tmap_ok = encode_feature_map(X, n, &tmap) ? 1 : 0;
+    k_mlp_forward_tc<<<grid, kTcThreads, sb, static_cast<cudaStream_t>(cuda_stream)>>>(to_dev(m), X, n, y, z1, tmap,
+                                                                                       tmap_ok);
     MHR_CUDA_TRY(cudaGetLastError());
     return MHR_OK;
 }

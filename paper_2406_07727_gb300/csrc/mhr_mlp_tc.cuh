@@ -26,7 +26,8 @@ struct MlpTcSmem {
     alignas(128) uint8_t B[kMlpHid * KC * 2];  // W1[:, 0:KC], K-major core-matrix layout
     alignas(128) uint8_t A[kTcRows * KC * 2];  // the tile's features, same layout
     float part[kTcRows][2];
-    uint64_t bar;
+    uint64_t bar;      // MMA completion
+    uint64_t tma_bar;  // TMA tile loads (the dense forward)
     uint32_t tmem;
     int failed;
 };
@@ -48,6 +49,7 @@ __device__ __forceinline__ void tc_setup(MlpTcSmem<KC>& sm) {
     if (threadIdx.x < 32) tc::tmem_alloc(&sm.tmem, kTcCols);
     if (threadIdx.x == 0) {
         tc::mbar_init(&sm.bar, 1);
+        tc::mbar_init(&sm.tma_bar, 1);
         tc::mbar_fence_init();
         sm.failed = 0;
     }
