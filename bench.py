@@ -234,7 +234,7 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ CPU oracle legs
-def cpu_oracle_rate(g, S, T, K, budget_s: float = 20.0, fn: str = "transe"):
+def cpu_oracle_rate(g, S, T, K, budget_s: float = 30.0, fn: str = "transe"):
     """The oracle (unchanged) on a bounded prefix sample of the queries.
     Returns (cpu_baseline dict, (n, paths, n_paths) of the last sample run)."""
     import oracle
