@@ -130,27 +130,7 @@ struct LevelArgs {
     unsigned long long* n_scored;  // edges scored (one counter)
     unsigned long long* n_exact;   // extensions scored in fp64 (one counter)
     double e1;                     // bound on |w32 - w64| of one edge
-    int G;                         // lanes per edge of the fp32 screen
 };
-
-// fp32 weight of the lane's own edge (x, r, y), computed by lane groups of G
-// (a power of two; 16-byte vector loads of the three rows), G edges of the
-// warp at a time; every lane of the warp calls.
-__device__ __forceinline__ float warp_edge_w32(const DevGraph& g, uint32_t x, uint32_t r, uint32_t y, int G) {
-    const int lane = threadIdx.x & 31, H = 32 / G, sub = lane & (G - 1);
-    const bool vec2 = g.dtype == MHR_F32 ? ((g.d & 3) == 0 && (g.d >> 2) <= 2 * G)
-                                         : ((g.d & 7) == 0 && (g.d >> 3) <= 2 * G);
-    float mine = 0.f;
-    for (int rd = 0; rd < G; ++rd) {
-        const int src = rd * H + lane / G;
-        const uint32_t rr = __shfl_sync(0xffffffffu, r, src);
-        const uint32_t yy = __shfl_sync(0xffffffffu, y, src);
-        const float w = vec2 ? edge_w32_group2(g, x, rr, yy, sub, G) : edge_w32_group(g, x, rr, yy, sub, G);
-        const float tw = __shfl_sync(0xffffffffu, w, ((lane - rd * H) & (H - 1)) * G);
-        if (lane / H == rd) mine = tw;
-    }
-    return mine;
-}
 
 // Screening of a path's extensions.  With T the K-th largest fp32 weight
 // w32 among them and E1 the bound on |w32 - w64|, every extension of the true
@@ -204,18 +184,15 @@ __global__ void __launch_bounds__(kBeamThreads) k_beam_level(LevelArgs a) {
             if (threadIdx.x == 0) c_top = 0u;
             __syncthreads();
             const int64_t e = base + threadIdx.x;
-            const bool live = threadIdx.x < kBeamChunk && e < e1;
-            uint32_t y = 0, r = 0;
-            bool cand = false;
-            if (live) {
-                y = a.g.col[e];
-                r = a.g.rel[e];
+            if (threadIdx.x < kBeamChunk && e < e1) {
+                const uint32_t y = a.g.col[e];
                 bool on_path = y == tq;
                 for (int i = 0; i <= a.level; ++i) on_path |= (p.v[i] == y);
-                cand = !on_path;
+                if (!on_path) {
+                    const float w = edge_w32_group(a.g, x, a.g.rel[e], y, 0, 1);
+                    if (w >= thr_adm) topw[n_top + atomicAdd(&c_top, 1u)] = w;
+                }
             }
-            const float w = warp_edge_w32(a.g, x, r, y, a.G);  // a dead lane scores vertex 0 (discarded)
-            if (cand && w >= thr_adm) topw[n_top + atomicAdd(&c_top, 1u)] = w;
             __syncthreads();
             const unsigned m = n_top + c_top;
             const bool last = base + kBeamChunk >= e1;
@@ -250,17 +227,15 @@ __global__ void __launch_bounds__(kBeamThreads) k_beam_level(LevelArgs a) {
         __syncthreads();
         // 1. score this chunk's edges; append behind the kept lists
         const int64_t e = base + threadIdx.x;
-        const bool live = threadIdx.x < kBeamChunk && e < e1;
-        const uint32_t y = live ? a.g.col[e] : 0u;
-        const uint32_t r = live ? a.g.rel[e] : 0u;
-        // the same fp32 weights as the screening pass (T is the same for the whole block)
-        const float w32 = T == -INFINITY ? 0.f : warp_edge_w32(a.g, x, r, y, a.G);
-        if (live) {
+        if (threadIdx.x < kBeamChunk && e < e1) {
+            const uint32_t y = a.g.col[e];
+            const uint32_t r = a.g.rel[e];
             bool on_path = false;
             for (int i = 0; i <= a.level; ++i) on_path |= (p.v[i] == y);
             if (!on_path && (y == tq || more)) {
                 // an extension outside the screening band cannot be among the K best
-                const bool keep = y == tq || T == -INFINITY || in_band(w32, T, p.score, a.e1);
+                const bool keep = y == tq || T == -INFINITY ||
+                                  in_band(edge_w32_group(a.g, x, r, y, 0, 1), T, p.score, a.e1);
                 if (keep) {
                     const double sc = __dadd_rn(p.score, edge_w64(a.g, x, r, y));
                     if (y == tq) res[n_rl + atomicAdd(&c_res, 1u)] = Ext{sc, y, r};
@@ -466,14 +441,6 @@ extern "C" mhr_status mhr_beam_paths(const mhr_graph* g, int32_t nq, const uint3
             a.n_scored = d_scored;
             a.n_exact = d_scored + 1;
             a.e1 = (g->eps32_edge + g->eps64_edge) * (1.0 + 1e-6);
-            {
-                // lanes per edge: about two 16-byte vectors of a row per lane
-                const int d = g->dg.d;
-                const int vec = g->dg.dtype == MHR_F32 ? ((d & 3) == 0 ? d / 4 : d) : ((d & 7) == 0 ? d / 8 : d);
-                int w = 1;
-                while (w < (vec + 1) / 2 && w < 32) w <<= 1;
-                a.G = w;
-            }
             k_beam_level<<<static_cast<unsigned>(qb * slots), kBeamThreads, 0, st>>>(a);
             std::swap(cur, nxt);
             slots *= K;
