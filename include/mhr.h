@@ -147,7 +147,7 @@ typedef struct {
 /* Query options; a NULL pointer means all defaults (zeros). */
 typedef struct {
     int32_t chunk;       /* edges per work item of the middle join: 0 = default (16384), else a
-                            multiple of 32 in [32, 16384] (MHR_EINVAL otherwise) */
+                            multiple of 32 in [32, 32768] (MHR_EINVAL otherwise) */
     int32_t order;       /* order of intermediate vertices: 0 natural, 1 by score
                             bound, 2 by score bound refined inside bound levels by
                             the learned slack prediction of `mlp` */
@@ -292,8 +292,8 @@ mhr_status mhr_merge_paths(int32_t nq, int32_t K, int32_t n_parts, const mhr_pat
  *   - middle-edge screen: opts->precision, or, when opts->precision < 0, both
  *     0 (fp32 CUDA cores) and 1 (bf16 tensor cores; only for DistMult with at
  *     most 16 relations);
- *   - work-item size chunks[i]: multiples of 32 in [32, 16384] (NULL:
- *     {4096, 8192, 16384}, n_chunks = 3);
+ *   - work-item size chunks[i]: multiples of 32 in [32, 32768] (NULL:
+ *     {8192, 16384, 32768}, n_chunks = 3);
  *   - scan tile tiles[j]: 4 or 8 (NULL: {4, 8}, n_tiles = 2).
  * Each combination gets one untimed run, then reps timed runs, timed by CUDA
  * events around the launch sequence on cuda_stream; ms_out (optional, host)

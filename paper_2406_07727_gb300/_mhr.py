@@ -443,7 +443,7 @@ def mhr_merge_paths(parts, n_parts_out, K: int, out=None, n_out=None, stream=Non
     return out, n_out
 
 
-def mhr_autotune(g: Graph, S, T, K: int, opts=None, chunks=(4096, 8192, 16384), tiles=(4, 8),
+def mhr_autotune(g: Graph, S, T, K: int, opts=None, chunks=(8192, 16384, 32768), tiles=(4, 8),
                  reps: int = 3, stream=None):
     """Time the batched search on (S, T) for every (screen, work-item size,
     scan tile) combination (both screens when opts["precision"] < 0); returns

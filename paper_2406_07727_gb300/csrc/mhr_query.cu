@@ -2450,6 +2450,7 @@ static mhr_status plan_alloc(Plan* p, T** out, size_t count) {
 }
 
 static size_t mid_smem_bytes() { return sizeof(MidSmem); }
+static_assert(sizeof(MidSmem) <= 232448, "the join's shared memory fits one CTA per SM (227 KB)");
 static size_t exact_smem_bytes() { return sizeof(ExactSmem); }
 static size_t merge2_smem_bytes(int band_cap) {
     int m = 2;
@@ -2802,7 +2803,7 @@ static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint
                             const mhr_query_opts* opts, cudaStream_t st, Plan** plan_out, bool label = false) {
     int chunk = (opts && opts->chunk > 0) ? opts->chunk : kDefaultChunk;
     if (chunk > kMaxChunk || chunk < 32 || (chunk & 31))
-        return fail(MHR_EINVAL, "opts->chunk must be a multiple of 32 in [32, 16384]");
+        return fail(MHR_EINVAL, "opts->chunk must be a multiple of 32 in [32, 32768]");
     const int precision = opts ? opts->precision : 0;
     if (precision != 0 && precision != 1) return fail(MHR_EINVAL, "opts->precision must be 0 or 1");
     const int tile = (opts && opts->tile) ? opts->tile : kDefaultTile;
@@ -2977,7 +2978,7 @@ extern "C" mhr_status mhr_autotune(const mhr_graph* gc, int32_t nq, const uint32
                                    int32_t* best_tile, int32_t* best_precision, float* ms_out, void* cuda_stream) {
     MHR_TRY(check_graph(gc));
     mhr_graph* G = const_cast<mhr_graph*>(gc);
-    static const int32_t kChunks[3] = {4096, 8192, 16384};
+    static const int32_t kChunks[3] = {8192, 16384, 32768};
     static const int32_t kTiles[2] = {4, 8};
     if (!chunks) {
         chunks = kChunks;
@@ -2994,7 +2995,7 @@ extern "C" mhr_status mhr_autotune(const mhr_graph* gc, int32_t nq, const uint32
     if (mem != MHR_MEM_HOST && mem != MHR_MEM_DEVICE) return fail(MHR_EINVAL, "unknown mem kind");
     for (int i = 0; i < n_chunks; ++i)
         if (chunks[i] > kMaxChunk || chunks[i] < 32 || (chunks[i] & 31))
-            return fail(MHR_EINVAL, "chunk candidates must be multiples of 32 in [32, 16384]");
+            return fail(MHR_EINVAL, "chunk candidates must be multiples of 32 in [32, 32768]");
     for (int i = 0; i < n_tiles; ++i)
         if (tiles[i] != 4 && tiles[i] != 8) return fail(MHR_EINVAL, "tile candidates must be 4 or 8");
     mhr_query_opts o = opts ? *opts : mhr_query_opts{};

@@ -11,7 +11,7 @@ namespace mhr {
 
 constexpr int kMidThreads = 1024;               // middle-join block (one per SM)
 constexpr int kMidWarps = kMidThreads / 32;
-constexpr int kMaxChunk = 16384;                // edges per work item, upper limit (<= 32 x threads)
+constexpr int kMaxChunk = 32768;                // edges per work item, upper limit (<= 32 x threads)
 constexpr int kDefaultChunk = 16384;
 static_assert(kMaxChunk / 32 <= kMidThreads, "one 32-edge group per thread in the group map");
 constexpr int kCandCap = 4096;                  // per-CTA fp32 candidate buffer

@@ -180,7 +180,7 @@ def test_topk_dyadic_many_ties_large_K(mhr):
 
 
 @pytest.mark.parametrize("prune,order", [(0, 0), (1, 0), (1, 1)])
-@pytest.mark.parametrize("chunk", [32, 64, 1024, 16384])
+@pytest.mark.parametrize("chunk", [32, 64, 1024, 16384, 32768])
 def test_topk_chunk_sizes(mhr, chunk, prune, order):
     """Work items of any size give the same answer (several items per query,
     ragged tails, hub rows split across items)."""
@@ -341,7 +341,7 @@ def test_work_counters_match_oracle(mhr):
     g.vemb, g.remb = synth.gen_embeddings(g.n, g.R, 16, 0.25, seed=14)
     S, T = synth.queries_edge_biased(g, 24, seed=14)
     G = mhr.load_kg(g)
-    for chunk in (64, 16384):
+    for chunk in (64, 16384, 32768):
         out, n_out, st = mhr.mhr_topk_paths_batched(G, S, T, 50, opts={"chunk": chunk}, with_stats=True)
         scanned = hits = paths = 0
         for s, t in zip(S.tolist(), T.tolist()):
