@@ -284,9 +284,11 @@ __device__ __forceinline__ void slot_commit(const PlanDev* __restrict__ P, const
     }
     // S_f / S_b: scan degrees of the distinct frontier vertices, summed per
     // (query, side) with one atomic per run of lanes sharing the key
+    // (the 32-bit degrees summed as two 16-bit halves, so the warp sums cannot overflow)
     const unsigned peers = __match_any_sync(0xffffffffu, key);
-    unsigned long long tot = 0ull;
-    for (unsigned m = peers; m; m &= m - 1) tot += __shfl_sync(peers, dsum, __ffs(m) - 1);
+    const uint32_t dd = static_cast<uint32_t>(dsum);
+    const unsigned long long tot = (static_cast<unsigned long long>(__reduce_add_sync(peers, dd >> 16)) << 16) +
+                                   __reduce_add_sync(peers, dd & 0xffffu);
     if (key != 0xffffffffu && lane == __ffs(peers) - 1 && tot) atomicAdd(&P->sdeg_q[key], tot);
 }
 
@@ -320,6 +322,227 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, D
             if (lane / H == rd) wmine = tw;
         }
         slot_commit(P, g, x, live, o, wmine, lane);
+    }
+}
+
+// Query of a slot at position lx of one side: the last q with offs[q] <= lx.
+// The warp's live slots are consecutive and on one side, so the warp finds
+// the query q0 of its first slot (position lx0) with a 32-ary search (three
+// rounds of one load per lane for 4,096 queries instead of twelve dependent
+// loads per lane), then each lane counts the query starts after q0 that are
+// <= lx among the next 32 (five shuffle steps).  A lane with more than 31
+// query starts between lx0 and lx (empty queries) searches on its own.
+__device__ __forceinline__ int warp_query_of(const int64_t* __restrict__ offs, int nq, int64_t lx0, int64_t lx,
+                                             int lane) {
+    int64_t lo = 0, span = static_cast<int64_t>(nq) + 1;  // offs[lo] <= lx0 < offs[lo + span] (or the end)
+    while (span > 32) {
+        const int64_t step = (span + 31) >> 5;
+        const int64_t j = lane * step;
+        const bool le = j < span && offs[lo + j] <= lx0;
+        const int64_t c = __popc(__ballot_sync(0xffffffffu, le));  // >= 1: offs[lo] <= lx0
+        const int64_t nlo = (c - 1) * step;
+        span = min(step, span - nlo);
+        lo += nlo;
+    }
+    {
+        const bool le = lane < span && offs[lo + lane] <= lx0;
+        lo += __popc(__ballot_sync(0xffffffffu, le)) - 1;
+    }
+    const int64_t j = lo + 1 + lane;
+    const int64_t b = j <= nq ? offs[j] : INT64_MAX;
+    int own = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int64_t pv = __shfl_sync(0xffffffffu, b, own + step - 1);
+        if (pv <= lx) own += step;
+    }
+    const int64_t b31 = __shfl_sync(0xffffffffu, b, 31);
+    if (b31 <= lx) return static_cast<int>(upper_bound_i64(offs, nq + 1, lx) - 1);
+    return static_cast<int>(lo) + own;
+}
+
+// slot_info without the scan degree, the query found warp-cooperatively.
+// All lanes call (the search uses the whole warp); lane 0 is live.
+__device__ __forceinline__ SlotInfo slot_locate_warp(const PlanDev* __restrict__ P, const DevGraph& g, int64_t x,
+                                                     bool live, int lane) {
+    SlotInfo o;
+    o.s = o.t = o.vtx = o.r = o.sdeg = 0;
+    o.prev = 0xffffffffu;
+    o.k = 0;
+    o.q = 0;
+    o.sideA = true;
+    const int64_t totA = P->totA;
+    const bool sA = x < totA;
+    const unsigned mC = __ballot_sync(0xffffffffu, live && !sA);
+    const unsigned mA = __ballot_sync(0xffffffffu, live && sA);
+    const bool uniform = mA == 0u || mC == 0u;  // warp-uniform
+    const int64_t lx = live ? (sA ? x : x - totA) : 0;
+    int q = 0;
+    if (uniform) {
+        const int64_t* offs = mC == 0u ? P->a_off : P->c_off;
+        const int64_t lx0 = __shfl_sync(0xffffffffu, lx, 0);
+        q = warp_query_of(offs, P->nq, lx0, live ? lx : lx0, lane);
+    } else if (live) {
+        q = static_cast<int>(upper_bound_i64(sA ? P->a_off : P->c_off, P->nq + 1, lx) - 1);
+    }
+    if (!live) return o;
+    const int64_t* offs = sA ? P->a_off : P->c_off;
+    o.sideA = sA;
+    o.q = q;
+    o.k = lx - offs[q];
+    o.s = P->S[q];
+    o.t = P->T[q];
+    if (sA) {
+        const int64_t p = g.off[o.s] + o.k;
+        o.vtx = g.col[p];
+        o.r = g.rel[p];
+        if (o.k > 0) o.prev = g.col[p - 1];
+    } else {
+        const int64_t p = g.roff[o.t] + o.k;
+        o.vtx = g.rcol[p];
+        o.r = g.rrel[p];
+        if (o.k > 0) o.prev = g.rcol[p - 1];
+    }
+    return o;
+}
+
+// k_expand for rows of at most two 16-byte vectors per lane of a G-lane group
+// (bf16 with d % 8 == 0 and d / 8 <= 2G, fp32 with d % 4 == 0 and d / 4 <=
+// 2G).  The rows of the random side (the slot's far endpoint) of up to four
+// rounds are loaded before any arithmetic, with the endpoint's scan-degree
+// loads beside them, so a warp keeps up to four rows per group in flight
+// instead of one; the fixed side (the query's s or t) and the relation row
+// are the same few rows for many slots and come from L1.  The group sums of
+// RB rounds are reduced together: plain xor steps down to RB lanes, then a
+// butterfly in which each step halves the rounds a lane carries, so lane
+// `sub` ends with round (sub mod RB): RB - 1 shuffles for the last log2(RB)
+// steps of RB rounds instead of RB log2(RB).  Every lane still adds its own partial to
+// its partner's at each step of the same xor tree, and fp32 addition is
+// commutative, so the weights equal those of edge_w32_group2 bit for bit.
+// Four rounds at a time and three 256-thread blocks per SM (80 registers)
+// measured fastest on the batching workload (3.31 ms per launch; eight rounds
+// at two blocks per SM 3.88 ms; two rounds at four blocks 3.32 ms).
+constexpr int kExpandRounds = 4;
+template <int G>
+__global__ void __launch_bounds__(256, 3) k_expand_v(const PlanDev* __restrict__ P, DevGraph g) {
+    constexpr int H = 32 / G;
+    constexpr int RB = G < kExpandRounds ? G : kExpandRounds;  // rounds loaded and reduced together
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (G - 1);
+    const int64_t X = P->X;
+    const int64_t warp_id = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const bool f32 = g.dtype == MHR_F32;
+    const bool transe = g.fn == MHR_SCORE_TRANSE_L1;
+    const int nvec = f32 ? (g.d >> 2) : (g.d >> 3);  // 16-byte vectors per row
+    const bool h0 = sub < nvec, h1 = sub + G < nvec;
+    const uint4* E = static_cast<const uint4*>(g.vemb);
+    const uint4* Rw = static_cast<const uint4*>(g.remb);
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t base = warp_id * 32; base < X; base += nwarps * 32) {  // warp-uniform
+        const int64_t x = base + lane;
+        const bool live = x < X;
+        SlotInfo o = slot_locate_warp(P, g, x, live, lane);
+        const uint32_t fixv = o.sideA ? o.s : o.t;               // dead lanes: vertex 0
+        const uint32_t rsa = (o.r << 1) | (o.sideA ? 1u : 0u);   // relation and side, one shuffle
+        const int64_t* so = o.sideA ? g.off : g.roff;
+        int64_t d0 = 0, d1 = 0;
+        if (live) {
+            d0 = so[o.vtx];
+            d1 = so[o.vtx + 1];
+        }
+        float wmine = 0.f;
+#pragma unroll
+        for (int rb = 0; rb < G; rb += RB) {
+            uint4 C0[RB], C1[RB];
+#pragma unroll
+            for (int i = 0; i < RB; ++i) {
+                const int src = (rb + i) * H + lane / G;
+                const int64_t v = __shfl_sync(FULL, o.vtx, src);
+                C0[i] = h0 ? __ldg(E + v * nvec + sub) : z;
+                C1[i] = h1 ? __ldg(E + v * nvec + sub + G) : z;
+            }
+            float acc[RB];
+#pragma unroll
+            for (int i = 0; i < RB; ++i) {
+                const int src = (rb + i) * H + lane / G;
+                const uint32_t q2 = __shfl_sync(FULL, rsa, src);
+                const int64_t rr = q2 >> 1;
+                const bool sa = (q2 & 1u) != 0u;
+                const int64_t fv = __shfl_sync(FULL, fixv, src);
+                const uint4 F0 = h0 ? __ldg(E + fv * nvec + sub) : z, B0 = h0 ? __ldg(Rw + rr * nvec + sub) : z;
+                const uint4 F1 = h1 ? __ldg(E + fv * nvec + sub + G) : z,
+                            B1 = h1 ? __ldg(Rw + rr * nvec + sub + G) : z;
+                // side A: the edge (s, r, vtx), head fixed; side C: (vtx, r, t), tail fixed
+                const uint4 As[2] = {sa ? F0 : C0[i], sa ? F1 : C1[i]};
+                const uint4 Cs[2] = {sa ? C0[i] : F0, sa ? C1[i] : F1};
+                const uint4 Bs[2] = {B0, B1};
+                float a_ = 0.f;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (k == 0 && !h0) break;
+                    if (k == 1 && !h1) break;
+                    const uint32_t a[4] = {As[k].x, As[k].y, As[k].z, As[k].w};
+                    const uint32_t b[4] = {Bs[k].x, Bs[k].y, Bs[k].z, Bs[k].w};
+                    const uint32_t c[4] = {Cs[k].x, Cs[k].y, Cs[k].z, Cs[k].w};
+                    if (f32) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            a_ += term_tr(__uint_as_float(a[e]), __uint_as_float(b[e]), __uint_as_float(c[e]), transe);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            a_ += term_tr(bf_lo(a[e]), bf_lo(b[e]), bf_lo(c[e]), transe);
+                            a_ += term_tr(bf_hi(a[e]), bf_hi(b[e]), bf_hi(c[e]), transe);
+                        }
+                    }
+                }
+                acc[i] = a_;
+            }
+            // xor steps G/2 .. RB: every round's sum over lanes that differ in those bits
+#pragma unroll
+            for (int off = G >> 1; off >= RB; off >>= 1)
+#pragma unroll
+                for (int i = 0; i < RB; ++i) acc[i] += __shfl_xor_sync(FULL, acc[i], off, G);
+            // butterfly over the low log2(RB) bits: keep the half of the rounds
+            // selected by this lane's bit, send the other half to the partner
+#pragma unroll
+            for (int off = RB >> 1; off > 0; off >>= 1) {
+                const bool hi = (sub & off) != 0;
+#pragma unroll
+                for (int j = 0; j < off; ++j) {
+                    const float send = hi ? acc[j] : acc[j + off];
+                    const float keep = hi ? acc[j + off] : acc[j];
+                    acc[j] = keep + __shfl_xor_sync(FULL, send, off, G);
+                }
+            }
+            // lane sub of group gi now holds round rb + (sub mod RB) of slot (round) * H + gi
+            const float w = transe ? __fsub_rn(g.gamma32, acc[0]) : acc[0];
+            const int rd = lane / H;
+            const float tw = __shfl_sync(FULL, w, (lane & (H - 1)) * G + (rd & (RB - 1)));
+            if (rd >= rb && rd < rb + RB) wmine = tw;
+        }
+        o.sdeg = static_cast<uint32_t>(d1 - d0);
+        slot_commit(P, g, x, live, o, wmine, lane);
+    }
+}
+
+using ExpandKernel = void (*)(const PlanDev*, DevGraph);
+
+// the expansion kernel for a graph's rows and group width
+static ExpandKernel expand_kernel(const DevGraph& g, int G) {
+    const bool vec2 = g.dtype == MHR_F32 ? ((g.d & 3) == 0 && (g.d >> 2) <= 2 * G)
+                                         : ((g.d & 7) == 0 && (g.d >> 3) <= 2 * G);
+    if (!vec2) return k_expand;
+    switch (G) {
+        case 1: return k_expand_v<1>;
+        case 2: return k_expand_v<2>;
+        case 4: return k_expand_v<4>;
+        case 8: return k_expand_v<8>;
+        case 16: return k_expand_v<16>;
+        case 32: return k_expand_v<32>;
+        default: return k_expand;
     }
 }
 
@@ -634,7 +857,7 @@ __global__ void k_order_perm(const PlanDev* __restrict__ P) {
 
 constexpr uint32_t kGposMulti = 0xffffffffu;   // group spans several near rows
 constexpr uint32_t kGposPruned = 0xfffffffeu;  // group inside one row whose bound misses the band
-constexpr int kSeedEdges = 16384;   // edges of each query's highest-bound rows done by the seed launch
+constexpr int kSeedEdges = 32768;   // edges of each query's highest-bound rows done by the seed launch
 constexpr int kSeedMinItems = 2;    // queries with fewer work items are not seeded
 
 // near entries in ordered position: (prefix of scan degree, row start), row
@@ -731,9 +954,6 @@ struct MidSmem {
     int nx_ready;
     int victim;     // offset of the range the CTA currently drains
     unsigned long long c_scanned, c_hits, c_cands, c_skipped;
-#ifdef MHR_PHASE_TIMING
-    unsigned long long sub[kMidWarps][6];  // per-warp cycles of the sub-phases (timing builds)
-#endif
 };
 
 // block-wide in-place compaction of the candidate buffer to s32 >= thr
@@ -897,12 +1117,21 @@ __device__ void setup_query(MidSmem& sm, const PlanDev* __restrict__ P, int q) {
     __syncthreads();
     if (sigma > 0) {
         // coarse bitmap (2^sigma vertices per bit): the far list is sorted by
-        // vertex, so the vertices of a set bit are contiguous in it; record
-        // where the run of each set bit starts, indexed by the bit's rank
-        uint2* fs = P->far_start + static_cast<int64_t>(blockIdx.x) * P->far_cap;
-        for (int k = threadIdx.x; k < sm.far_cnt; k += blockDim.x) {
+        // vertex, so the vertices of a set bit are contiguous in it; record,
+        // indexed by the bit's rank, the run's first entry and vertex (written
+        // by the thread at the run's start) and its last vertex and entry
+        // (written by the thread at its end: the other 8-byte half)
+        uint2* fs = reinterpret_cast<uint2*>(P->far_start + static_cast<int64_t>(blockIdx.x) * P->far_cap);
+        const int fc = sm.far_cnt;
+        for (int k = threadIdx.x; k < fc; k += blockDim.x) {
             const uint32_t fv = far[k].vertex, bv = fv >> sigma;
-            if (k == 0 || (far[k - 1].vertex >> sigma) != bv) fs[bm_rank(sm, bv)] = make_uint2(static_cast<uint32_t>(k), fv);
+            const bool first = k == 0 || (far[k - 1].vertex >> sigma) != bv;
+            const bool last = k == fc - 1 || (far[k + 1].vertex >> sigma) != bv;
+            if (first || last) {
+                const uint32_t r = bm_rank(sm, bv);
+                if (first) fs[2 * r] = make_uint2(static_cast<uint32_t>(k), fv);
+                if (last) fs[2 * r + 1] = make_uint2(fv, static_cast<uint32_t>(k));
+            }
         }
         __syncthreads();
     }
@@ -1262,12 +1491,12 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
 #define MHR_WEND(acc) ((acc) += clock64() - t_w)
 #define MHR_COUNT(c) (++(c))
     unsigned long long t_sub = 0;
-    for (int i = threadIdx.x; i < kMidWarps * 6; i += blockDim.x) (&sm.sub[0][0])[i] = 0ull;
+    unsigned long long subc[6] = {0, 0, 0, 0, 0, 0};  // this warp's cycles of the sub-phases (lane 0)
 #define MHR_SUB_START() (t_sub = clock64())
 #define MHR_SUB(i)                                               \
     do {                                                         \
         const unsigned long long now__ = clock64();              \
-        if (lane == 0) sm.sub[warp][i] += now__ - t_sub;        \
+        if (lane == 0) subc[i] += now__ - t_sub;                 \
         t_sub = now__;                                           \
     } while (0)
 #else
@@ -1474,7 +1703,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         const uint32_t* colsrc = sm.dir ? g.col : g.rcol;
         const ListEnt* far = P->list + sm.far_base;
         const int far_cnt = sm.far_cnt;
-        const uint2* far_start = P->far_start + static_cast<int64_t>(blockIdx.x) * P->far_cap;
+        const uint4* far_start = P->far_start + static_cast<int64_t>(blockIdx.x) * P->far_cap;
         const uint16_t* relsrc = sm.dir ? g.rel : g.rrel;
         MHR_WSTART();
         for (int gb = warp * UNROLL; gb < ngroups; gb += kMidWarps * UNROLL) {
@@ -1573,26 +1802,32 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                 }
             }
             if (sigma > 0) {
-                // coarse bitmap: the set bit's run in the far list starts at far_start[rank]
-                // (written by this CTA's query set-up: a coherent load), which also
-                // holds the run's first vertex
-                uint32_t fv[UNROLL];
+                // coarse bitmap: far_start[rank] (written by this CTA's query set-up:
+                // a coherent load) holds the set bit's run in the far list: first
+                // entry and vertex, last vertex and entry.  x equal to either end is
+                // a hit, x outside them a miss; only x strictly inside a run of three
+                // or more walks the run.
+                bool walk[UNROLL];
 #pragma unroll
                 for (int u = 0; u < UNROLL; ++u) {
-                    fv[u] = 0u;
+                    walk[u] = false;
                     if (hit[u]) {
-                        const uint2 st = far_start[fk[u]];
-                        fk[u] = st.x;
-                        fv[u] = st.y;
+                        const uint4 st = far_start[fk[u]];
+                        const uint32_t x = xv[u];
+                        walk[u] = st.y < x && x < st.z;
+                        hit[u] = x == st.y || x == st.z;
+                        fk[u] = x == st.z ? st.w : st.x;
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < UNROLL; ++u) {
-                    if (!hit[u]) continue;
+                    if (!walk[u]) continue;
                     const uint32_t x = xv[u];
-                    uint32_t k = fk[u], v = fv[u];
-                    while (v < x && ++k < static_cast<uint32_t>(far_cnt)) v = far[k].vertex;
-                    hit[u] = k < static_cast<uint32_t>(far_cnt) && v == x;
+                    uint32_t k = fk[u], v = 0u;
+                    do {
+                        v = far[++k].vertex;
+                    } while (v < x);
+                    hit[u] = v == x;
                     fk[u] = k;
                 }
             }
@@ -1906,10 +2141,15 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
             atomicAdd(&wr[3], wt_score);
         }
         __syncthreads();
+        __syncthreads();
+        if (threadIdx.x < 6) wr[4 + threadIdx.x] = 0ull;
+        __syncthreads();
+        if (lane == 0)
+            for (int i = 0; i < 6; ++i) atomicAdd(&wr[4 + i], subc[i]);
+        __syncthreads();
         if (threadIdx.x == 0) {
-            unsigned long long a[6] = {0, 0, 0, 0, 0, 0};
-            for (int w = 0; w < kMidWarps; ++w)
-                for (int i = 0; i < 6; ++i) a[i] += sm.sub[w][i];
+            unsigned long long a[6];
+            for (int i = 0; i < 6; ++i) a[i] = wr[4 + i];
             printf("MHR_SUB %d %d nearP %llu col_bitmap_hits %llu hit_load %llu w2 %llu combos %llu\n", blockIdx.x,
                    SEED ? 1 : 0, a[0] / kMidWarps, a[1] / kMidWarps, a[2] / kMidWarps, a[3] / kMidWarps,
                    a[4] / kMidWarps);
@@ -2361,7 +2601,8 @@ __global__ void k_dump_labels(const PlanDev* __restrict__ P, int64_t cap, uint32
 // ===========================================================================
 struct Plan {
     int nq = 0, K = 0, chunk = 0, grid = 0, precision = 0, tile = kDefaultTile;
-    int expand_per_sm = 8;  // resident k_expand blocks per SM
+    int expand_per_sm = 8;  // resident expansion blocks per SM
+    void (*expand_fn)(const PlanDev*, DevGraph) = nullptr;  // the expansion kernel for the graph's rows
     PlanDev h{};
     unsigned char* dregion = nullptr;  // [PlanDev][S][T][a_off][c_off]
     size_t region_bytes = 0;
@@ -2525,14 +2766,14 @@ static mhr_status ensure_far(Plan* p, int64_t cap) {
     if (cap <= p->h.far_cap && p->h.far_start) return MHR_OK;
     cap = std::max(cap, 2 * p->h.far_cap);
     void* mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, sizeof(uint2) * static_cast<size_t>(cap) * p->grid);
+    cudaError_t e = cudaMalloc(&mem, sizeof(uint4) * static_cast<size_t>(cap) * p->grid);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (far-set run starts)");
     if (p->far_mem) {
         cudaDeviceSynchronize();
         cudaFree(p->far_mem);
     }
     p->far_mem = mem;
-    p->h.far_start = static_cast<uint2*>(mem);
+    p->h.far_start = static_cast<uint4*>(mem);
     p->h.far_cap = cap;
     return MHR_OK;
 }
@@ -2565,7 +2806,7 @@ static cudaError_t launch_part(Plan* p, const mhr_graph* G, cudaStream_t st, int
         k_init<<<sms * 2, 256, 0, st>>>(d, g);
         cudaError_t ee = cudaEventRecordWithFlags(p->ev_x[0], st, cudaEventRecordExternal);
         if (ee != cudaSuccess) return ee;
-        k_expand<<<sms * p->expand_per_sm, 256, 0, st>>>(d, g);
+        p->expand_fn<<<sms * p->expand_per_sm, 256, 0, st>>>(d, g);
         ee = cudaEventRecordWithFlags(p->ev_x[1], st, cudaEventRecordExternal);
         if (ee != cudaSuccess) return ee;
         cudaError_t e = device_excl_scan<uint32_t>(p->h.flag, nX, p->h.partials, p->h.scan1, st);
@@ -2762,7 +3003,8 @@ static mhr_status make_plan(mhr_graph* G, int nq, int K, int chunk, int precisio
     {
         // one resident wave of the grid-stride expansion kernel
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_expand, 256, 0) == cudaSuccess && nb > 0)
+        p->expand_fn = expand_kernel(G->dg, h.score_width);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, p->expand_fn, 256, 0) == cudaSuccess && nb > 0)
             p->expand_per_sm = nb;
         cudaGetLastError();
     }

@@ -148,8 +148,8 @@ struct PlanDev {
     unsigned long long* counters;  // kCntCount
     unsigned long long* cursors;   // [grid] next item of each CTA's own range
     uint32_t* drained;             // [(grid + 31) / 32] bit v: range v has no item left
-    uint2* far_start;              // [grid x far_cap] coarse bitmap: (far-list start, its vertex) of
-                                   // each set bit's run
+    uint4* far_start;              // [grid x far_cap] coarse bitmap, per set bit's run in the far list:
+                                   // (first entry, its vertex, last vertex, its entry)
     int64_t far_cap;               // longest far list of the batch (coarse bitmaps only)
     int64_t* partials;             // scan scratch
 };
