@@ -235,6 +235,37 @@ def test_large_vertex_count_coarse_bitmap(mhr):
     run_and_compare(mhr, g, S, T, 50, "transe", opts={"prune": 1, "order": 1, "chunk": 256})
 
 
+@pytest.mark.parametrize("opts", [None, {"prune": 1, "order": 1}])
+def test_many_small_and_empty_queries(mhr, opts):
+    """A batch of 600 queries whose sources have out-degree 0, 1 or 2 and whose
+    targets have in-degree 0, 1 or 2: a warp's 32 expansion slots span dozens
+    of query starts (several with no slot at all), so the warp's query search
+    takes both its shuffle path and the per-lane fallback; results still
+    match the oracle query by query."""
+    rng = np.random.default_rng(31)
+    n, R = 1500, 3
+    src, dst = [], []
+    for s in range(0, 500):                       # low-degree sources 0..499
+        for _ in range(int(rng.integers(0, 3))):
+            src.append(s); dst.append(int(rng.integers(500, 1000)))
+    for _ in range(80000):                        # middle edges among 500..999
+        src.append(int(rng.integers(500, 1000))); dst.append(int(rng.integers(500, 1000)))
+    for t in range(1000, 1500):                   # low in-degree targets 1000..1499
+        for _ in range(int(rng.integers(0, 3))):
+            src.append(int(rng.integers(500, 1000))); dst.append(t)
+    rel = rng.integers(0, R, len(src))
+    offsets, cols, rels = synth.canonicalize(n, R, np.array(src), rel, np.array(dst))
+    vemb = (rng.standard_normal((n, 8)) * 0.4).astype(np.float32)
+    remb = (rng.standard_normal((R, 8)) * 0.4).astype(np.float32)
+    g = synth.KG(n=n, R=R, n_types=1, offsets=offsets, cols=cols, rels=rels,
+                 vtypes=np.zeros(n, dtype=np.uint8), vemb=vemb, remb=remb, dtype="f32")
+    S = rng.integers(0, 500, 600).astype(np.uint32)
+    T = rng.integers(1000, 1500, 600).astype(np.uint32)
+    deg = np.diff(g.offsets)
+    assert (deg[S] == 0).sum() > 100 and (deg[S] == 2).sum() > 100
+    run_and_compare(mhr, g, S, T, 20, "transe", opts=opts)
+
+
 def test_coarse_bitmap_dense_runs(mhr):
     """A coarse bitmap whose set bits cover runs of several far vertices: a
     hub target whose in-neighbours are consecutive vertex ids."""
