@@ -62,6 +62,10 @@ WORKLOAD_DESCS = {
     "batching": ("R-MAT (a,b,c)=(.57,.19,.19) typed KG: 10,000,000 vertices, 200,000,000 edges, "
                  "32 relations, 6 vertex types, d=128 bf16 embeddings ~N(0,1/sqrt(d)); 4,096 queries "
                  "per step with log-uniform source degree in [1,1e5], K=50, TransE-L1 (gamma=1)"),
+    "batching_quarter": ("the batching recipe at a quarter of its size (the profiler-capture case): R-MAT "
+                         "(a,b,c)=(.57,.19,.19) typed KG: 2,500,000 vertices, 50,000,000 edges, 32 relations, "
+                         "6 vertex types, d=128 bf16 embeddings ~N(0,1/sqrt(d)); 1,024 queries per step with "
+                         "log-uniform source degree in [1,1e5], K=50, TransE-L1 (gamma=1)"),
     "tiny": ("Zipf(2.1) typed KG: 10,000 vertices, 100,000 edges, 8 relations, d=64 fp32 ~N(0,1/8); "
              "one hub query, K=10, TransE-L1"),
     "precision": ("the medium R-MAT graph (1,000,000 vertices, 20,000,000 edges, 16 relations) with d=256 "
@@ -84,7 +88,7 @@ FORM_DESC = {"plain": "plain: batched, every middle edge scored, fp32 screen + f
                       "bound pruning of work items, rows and hits (identical output)",
              "chosen": "chosen: as bound, with rows ordered by the learned MLP score (trained on plain runs "
                        "over 20,000 held-out queries before timing) (identical output)"}
-# kernels per step: k_init, k_expand, scan x2, k_lists, k_plan, k_order_key, k_mlp_qbias,
+# kernels per step: k_init, k_expand_v, scan x2, k_lists, k_plan, k_order_key, k_mlp_qbias,
 # k_mlp_keys, k_order_hist, scan x2, k_order_perm, scan x2, k_near, k_middle (seed),
 # k_middle, k_merge1, k_rescore, k_merge2, k_exact
 KERNELS_PER_STEP = 22
@@ -94,8 +98,8 @@ KERNELS_PER_STEP = 22
 TRAFFIC_NCU = {# batching workload, main join launch of the second call, one
                # capture each of the current kernel (1 pass: dram__bytes_read.sum
                # + dram__bytes_write.sum at full size)
-               ("batching", "chosen", 16384, 4): 89_140_000_000,
-               ("batching", "bound", 16384, 4): 89_450_000_000}
+               ("batching", "chosen", 32768, 4): 100_890_000_000,
+               ("batching", "bound", 32768, 4): 101_060_000_000}
 
 
 def dist_env():
@@ -111,7 +115,7 @@ def rank_queries(g, S, T, rank: int, workload: str):
     import synth
     if rank == 0:
         return S, T
-    if workload == "batching":
+    if synth.WORKLOADS[workload]["queries"] == "logdeg":
         return synth.queries_log_degree(g, len(S), seed=rank)
     return synth.queries_edge_biased(g, len(S), seed=rank)
 
@@ -640,7 +644,7 @@ def run_gpu(args):
         t0 = time.perf_counter()
         import synth
         # training queries: the workload's own recipe on stream 3 (disjoint from the timed ones)
-        if WORKLOAD == "batching":
+        if synth.WORKLOADS[WORKLOAD]["queries"] == "logdeg":
             St, Tt = synth.queries_log_degree(g, args.train_queries, seed=rank, stream=3)
         else:
             St, Tt = synth.queries_edge_biased(g, args.train_queries, seed=rank, stream=3)

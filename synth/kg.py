@@ -320,6 +320,11 @@ WORKLOADS = {
     # 4096 queries with log-uniform source degree in [1, 1e5], K = 50
     "batching": dict(kind="rmat", scale=24, n=10_000_000, E=200_000_000, R=32, n_types=6, d=128,
                      var=None, dtype="bf16", queries="logdeg", nq=4096, K=50, score="transe"),
+    # the batching recipe at a quarter of its size (about 2 GB on the device: the
+    # case for full-metric profiler captures): R-MAT scale 22 cut to 2.5M vertices,
+    # 50M edges, 1,024 log-degree queries, K = 50
+    "batching_quarter": dict(kind="rmat", scale=22, n=2_500_000, E=50_000_000, R=32, n_types=6, d=128,
+                             var=None, dtype="bf16", queries="logdeg", nq=1024, K=50, score="transe"),
 }
 
 
