@@ -95,11 +95,11 @@ KERNELS_PER_STEP = 22
 # DRAM bytes (read + write) of one main join launch from one ncu capture of the
 # current kernel, per (workload, form, work-item size, scan tile); any other
 # configuration reports null.
-TRAFFIC_NCU = {# batching workload, main join launch of the second call, one
+TRAFFIC_NCU = {# batching workload: the main join launch of one timed step, one
                # capture each of the current kernel (1 pass: dram__bytes_read.sum
-               # + dram__bytes_write.sum at full size)
-               ("batching", "chosen", 32768, 4): 100_890_000_000,
-               ("batching", "bound", 32768, 4): 101_060_000_000}
+               # + dram__bytes_write.sum at full size, --profile-range)
+               ("batching", "chosen", 32768, 4): 101_110_000_000,
+               ("batching", "bound", 32768, 4): 100_820_000_000}
 
 
 def dist_env():
@@ -346,12 +346,16 @@ def run_reference(args):
     else:
         g, S, T, K, spec = load_workload(0)
     fn = spec.get("score", "transe") if WORKLOAD not in ("tail", "beam") else "transe"
-    # Every step runs one batch of queries through the oracle (OpenMP over the
-    # batch, dynamic schedule).  The batch is sized once, by doubling from one
-    # query per thread, until a batch takes the per-step budget; steps walk
-    # through the workload's queries in windows of that size.
+    # Every step runs the same batch of queries through the oracle (OpenMP over
+    # the batch, dynamic schedule): queries spaced evenly through the workload's
+    # list, so the sample spans its degree mix.  The batch is sized once, by
+    # doubling from one query per thread until a batch takes the per-step
+    # budget, so the whole run stays within a few minutes.
     cores = oracle.num_threads()
     budget = min(6.0, max(0.3, 150.0 / (args.warmup + args.steps)))
+
+    def sample(m):
+        return np.unique(np.linspace(0, len(S) - 1, m).round().astype(np.int64))
 
     def run(idx):
         t0 = time.perf_counter()
@@ -364,13 +368,12 @@ def run_reference(args):
         return time.perf_counter() - t0
 
     per_step = max(1, min(len(S), cores))
-    while per_step < len(S) and run(np.arange(per_step)) < budget:
+    while per_step < len(S) and run(sample(per_step)) < budget:
         per_step = min(len(S), 2 * per_step)
+    idx = sample(per_step)
+    per_step = len(idx)
     times = []
-    qi = 0
     for step in range(args.warmup + args.steps):
-        idx = np.arange(qi, qi + per_step) % len(S)
-        qi += per_step
         dt = run(idx)
         if step >= args.warmup:
             times.append(dt)
@@ -386,7 +389,8 @@ def run_reference(args):
                                 f"CPU oracle: fp64 brute force, OpenMP over the step's {per_step} queries")},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} queries per step (one batch, sized to about {budget:.1f} s), "
-                                       f"windows walking through the {len(S)} workload queries"},
+                                       f"spaced evenly through the {len(S)} workload queries, the same "
+                                       f"batch every step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

@@ -1460,7 +1460,7 @@ __device__ void select_item(MidSmem& sm, const PlanDev* __restrict__ P, int nq, 
 // shared K-th score of every query is set before the main launch starts.
 template <int UNROLL, bool SEED, bool TC>
 __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __restrict__ P, DevGraph g) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     MidSmem& sm = *reinterpret_cast<MidSmem*>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int K = P->K;
@@ -1702,7 +1702,6 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
         // --- scan: stream near rows, probe the far bitmap, stage hits
         const uint32_t* colsrc = sm.dir ? g.col : g.rcol;
         const ListEnt* far = P->list + sm.far_base;
-        const int far_cnt = sm.far_cnt;
         const uint4* far_start = P->far_start + static_cast<int64_t>(blockIdx.x) * P->far_cap;
         const uint16_t* relsrc = sm.dir ? g.rel : g.rrel;
         MHR_WSTART();
@@ -2370,7 +2369,7 @@ __global__ void __launch_bounds__(kRsWarps * 32) k_rescore(const PlanDev* __rest
 }
 
 __global__ void __launch_bounds__(1024) k_merge2(const PlanDev* __restrict__ P, DevGraph g) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     mhr_path* buf = reinterpret_cast<mhr_path*>(smem_raw);
     const int K = P->K;
     for (int q = blockIdx.x; q < P->nq; q += gridDim.x) {
@@ -2447,7 +2446,7 @@ __device__ void exact_flush(ExactSmem& sm, int K) {
 }
 
 __global__ void __launch_bounds__(1024) k_exact(const PlanDev* __restrict__ P, DevGraph g) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     ExactSmem& sm = *reinterpret_cast<ExactSmem*>(smem_raw);
     const int K = P->K;
     const double err = P->err_path;

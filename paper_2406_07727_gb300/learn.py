@@ -143,3 +143,36 @@ def train_ordering_mlp(G, S, T, epochs: int = 3, batch: int = 4096, lr: float = 
     model.fold_target_scale(mean, std)
     return model, TrainReport(rows=n, epochs=epochs, loss_first=losses[0], loss_last=losses[-1],
                               target_mean=mean, target_std=std)
+
+
+def time_forward(rows: int = 262_144, repeat: int = 10, warmup: int = 3, seed: int = 1) -> dict:
+    """CUDA-event time of the network's dense forward (TMA + tcgen05) over
+    `rows` random bf16 feature rows, without the pre-activation output (the
+    form the order keys use); returns microseconds per call and TFLOP/s of
+    the first layer's 2 x 256 x 256 flops per row."""
+    import torch
+    model = OrderingMLP(seed=seed)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    X = torch.randn((rows, 256), generator=g, device="cuda").to(torch.bfloat16).view(torch.int16)
+    y = torch.empty(rows, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        _mhr.mhr_mlp_forward(model, X, y)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(repeat):
+        _mhr.mhr_mlp_forward(model, X, y)
+    t1.record()
+    torch.cuda.synchronize()
+    us = t0.elapsed_time(t1) * 1e3 / repeat
+    return {"rows": rows, "us_per_call": us, "tflops": 2.0 * 256 * 256 * rows / (us * 1e-6) / 1e12}
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="time the ordering MLP's dense forward on the GPU")
+    ap.add_argument("--rows", type=int, default=262_144)
+    ap.add_argument("--repeat", type=int, default=10)
+    a = ap.parse_args()
+    print(json.dumps(time_forward(a.rows, a.repeat)))
