@@ -198,53 +198,12 @@ __device__ __forceinline__ float edge_w32_group(const DevGraph& g, uint32_t u, u
     return acc;
 }
 
-// edge_w32_group for rows of at most two 16-byte vectors per lane (fp32 with
-// d % 4 == 0 and d / 4 <= 2 * width, or bf16 with d % 8 == 0 and
-// d / 8 <= 2 * width): all six row loads are issued before any arithmetic.
+// bf16 halves of a 32-bit word widened to fp32, and one TransE-L1 / DistMult term
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
 __device__ __forceinline__ float term_tr(float a, float b, float c, bool transe) {
     return transe ? fabsf(__fsub_rn(__fadd_rn(a, b), c)) : (a * b) * c;
-}
-
-__device__ __forceinline__ float edge_w32_group2(const DevGraph& g, uint32_t u, uint32_t r, uint32_t v, int lane,
-                                                 int width) {
-    const int d = g.d;
-    const bool transe = g.fn == MHR_SCORE_TRANSE_L1;
-    const int nvec = g.dtype == MHR_F32 ? (d >> 2) : (d >> 3);
-    const bool h0 = lane < nvec, h1 = lane + width < nvec;
-    const int esz = g.dtype == MHR_F32 ? 4 : 2;
-    const uint4* eu = reinterpret_cast<const uint4*>(static_cast<const char*>(g.vemb) + static_cast<int64_t>(u) * d * esz);
-    const uint4* wr = reinterpret_cast<const uint4*>(static_cast<const char*>(g.remb) + static_cast<int64_t>(r) * d * esz);
-    const uint4* ev = reinterpret_cast<const uint4*>(static_cast<const char*>(g.vemb) + static_cast<int64_t>(v) * d * esz);
-    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-    const uint4 A0 = h0 ? __ldg(eu + lane) : z, B0 = h0 ? __ldg(wr + lane) : z, C0 = h0 ? __ldg(ev + lane) : z;
-    const uint4 A1 = h1 ? __ldg(eu + lane + width) : z, B1 = h1 ? __ldg(wr + lane + width) : z,
-                C1 = h1 ? __ldg(ev + lane + width) : z;
-    float acc = 0.f;
-    const uint4 As[2] = {A0, A1}, Bs[2] = {B0, B1}, Cs[2] = {C0, C1};
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        if (k == 1 && !h1) break;
-        if (k == 0 && !h0) break;
-        const uint32_t a[4] = {As[k].x, As[k].y, As[k].z, As[k].w};
-        const uint32_t b[4] = {Bs[k].x, Bs[k].y, Bs[k].z, Bs[k].w};
-        const uint32_t c[4] = {Cs[k].x, Cs[k].y, Cs[k].z, Cs[k].w};
-        if (g.dtype == MHR_F32) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                acc += term_tr(__uint_as_float(a[i]), __uint_as_float(b[i]), __uint_as_float(c[i]), transe);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                acc += term_tr(bf_lo(a[i]), bf_lo(b[i]), bf_lo(c[i]), transe);
-                acc += term_tr(bf_hi(a[i]), bf_hi(b[i]), bf_hi(c[i]), transe);
-            }
-        }
-    }
-    for (int o = width >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, width);
-    return transe ? __fsub_rn(g.gamma32, acc) : acc;
 }
 
 // Edge weight in fp64, canonical order: j = 0..d-1 sequentially, explicit

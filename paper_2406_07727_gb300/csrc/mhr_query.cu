@@ -302,9 +302,6 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, D
     const int64_t X = P->X;
     const int64_t warp_id = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    // rows of at most two 16-byte vectors per lane: unrolled scorer
-    const bool vec2 = g.dtype == MHR_F32 ? ((g.d & 3) == 0 && (g.d >> 2) <= 2 * G)
-                                         : ((g.d & 7) == 0 && (g.d >> 3) <= 2 * G);
     for (int64_t base = warp_id * 32; base < X; base += nwarps * 32) {  // warp-uniform
         const int64_t x = base + lane;
         const bool live = x < X;
@@ -317,7 +314,7 @@ __global__ void __launch_bounds__(256) k_expand(const PlanDev* __restrict__ P, D
             const uint32_t rr = __shfl_sync(0xffffffffu, o.r, src);
             const uint32_t b = __shfl_sync(0xffffffffu, tv, src);
             // dead lanes score vertex 0's rows
-            const float w = vec2 ? edge_w32_group2(g, a, rr, b, sub, G) : edge_w32_group(g, a, rr, b, sub, G);
+            const float w = edge_w32_group(g, a, rr, b, sub, G);
             const float tw = __shfl_sync(0xffffffffu, w, ((lane - rd * H) & (H - 1)) * G);
             if (lane / H == rd) wmine = tw;
         }
@@ -418,7 +415,8 @@ __device__ __forceinline__ SlotInfo slot_locate_warp(const PlanDev* __restrict__
 // `sub` ends with round (sub mod RB): RB - 1 shuffles for the last log2(RB)
 // steps of RB rounds instead of RB log2(RB).  Every lane still adds its own partial to
 // its partner's at each step of the same xor tree, and fp32 addition is
-// commutative, so the weights equal those of edge_w32_group2 bit for bit.
+// commutative, so with the same per-element expression and the same order
+// within a lane the weights are those edge_w32_group computes.
 // Four rounds at a time and three 256-thread blocks per SM (80 registers)
 // measured fastest on the batching workload (3.31 ms per launch; eight rounds
 // at two blocks per SM 3.88 ms; two rounds at four blocks 3.32 ms).
