@@ -179,6 +179,48 @@ def test_topk_dyadic_many_ties_large_K(mhr):
     run_and_compare(mhr, g, S, T, 100, "distmult")
 
 
+@pytest.mark.parametrize("opts", [{"prune": 1, "order": 1}, {"prune": 1, "order": 1, "chunk": 256}])
+def test_topk_dyadic_ties_largest_K_pruned(mhr, opts):
+    """K = 1024 (the largest K) with bound pruning, on dyadic embeddings where
+    many paths tie: the kept band and the tie order at the K-th score are
+    decided with pruning on, in small and large work items."""
+    rng = np.random.default_rng(18)
+    g = random_kg(rng, 400, 30000, 2, 2, dyadic=True)
+    S = rng.integers(0, 400, 16).astype(np.uint32)
+    T = rng.integers(0, 400, 16).astype(np.uint32)
+    run_and_compare(mhr, g, S, T, mhr.MHR_K_MAX, "transe", opts=opts)
+
+
+def test_duplicate_queries_in_one_batch(mhr):
+    """The same hub query 40 times in one batch (and its reverse 40 times), in
+    64-edge work items: CTAs take and steal items of many copies at once, each
+    copy keeps its own threshold and candidates, and every copy returns the
+    oracle's list."""
+    rng = np.random.default_rng(19)
+    g = random_kg(rng, 300, 12000, 4, 16)
+    deg_out, deg_in = np.diff(g.offsets), np.bincount(g.cols, minlength=g.n)
+    s = int(np.argmax(deg_out))
+    t = int(np.argmax(np.where(np.arange(g.n) == s, -1, deg_in)))
+    S = np.array([s] * 40 + [t] * 40, dtype=np.uint32)
+    T = np.array([t] * 40 + [s] * 40, dtype=np.uint32)
+    out, n_out = run_and_compare(mhr, g, S, T, 60, "transe", opts={"prune": 1, "order": 1, "chunk": 64})
+    for q in range(1, 40):
+        assert out[q][: n_out[q]].tobytes() == out[0][: n_out[0]].tobytes()
+        assert out[40 + q][: n_out[40 + q]].tobytes() == out[40][: n_out[40]].tobytes()
+
+
+@pytest.mark.parametrize("opts", [None, {"prune": 1, "order": 1}])
+def test_more_queries_than_a_block(mhr, opts):
+    """5,000 queries in one batch: more queries than one 1,024-thread block of
+    the planning kernels covers per pass, so their block-wide scans carry
+    across passes; every query is compared with the oracle."""
+    rng = np.random.default_rng(20)
+    g = random_kg(rng, 2000, 40000, 3, 8)
+    S = rng.integers(0, 2000, 5000).astype(np.uint32)
+    T = rng.integers(0, 2000, 5000).astype(np.uint32)
+    run_and_compare(mhr, g, S, T, 10, "transe", opts=opts)
+
+
 @pytest.mark.parametrize("prune,order", [(0, 0), (1, 0), (1, 1)])
 @pytest.mark.parametrize("chunk", [32, 64, 1024, 16384, 32768])
 def test_topk_chunk_sizes(mhr, chunk, prune, order):
