@@ -227,7 +227,10 @@ def _opts(opts, n_relations: int = 0) -> Optional[QueryOpts]:
     if isinstance(opts, QueryOpts):
         return opts
     o = QueryOpts()
+    known = {name for name, _ in QueryOpts._fields_} - {"reserved"}
     for k, v in dict(opts).items():
+        if k not in known:
+            raise ValueError(f"unknown query option {k!r} (known: {', '.join(sorted(known))})")
         if k == "mlp":
             o._mlp_keep = v if isinstance(v, MLP) else v.struct()
             o.mlp = ctypes.pointer(o._mlp_keep)
@@ -248,6 +251,9 @@ def _constraints(c, n_relations: int) -> Constraints:
     if isinstance(c, Constraints):
         return c
     c = dict(c)
+    unknown = set(c) - {"rel1", "rel2", "rel3", "types_u", "types_v"}
+    if unknown:
+        raise ValueError(f"unknown constraint {sorted(unknown)[0]!r} (known: rel1, rel2, rel3, types_u, types_v)")
     n_rel = int(n_relations)
     out = Constraints()
     keep = []
