@@ -95,11 +95,7 @@ KERNELS_PER_STEP = 22
 # DRAM bytes (read + write) of one main join launch from one ncu capture of the
 # current kernel, per (workload, form, work-item size, scan tile); any other
 # configuration reports null.
-TRAFFIC_NCU = {# batching workload: the main join launch of one timed step, one
-               # capture each of the current kernel (1 pass: dram__bytes_read.sum
-               # + dram__bytes_write.sum at full size, --profile-range)
-               ("batching", "chosen", 32768, 4): 101_110_000_000,
-               ("batching", "bound", 32768, 4): 100_820_000_000}
+TRAFFIC_NCU = {}  # filled from a capture of the current kernel only
 
 
 def dist_env():

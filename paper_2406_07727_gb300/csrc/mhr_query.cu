@@ -1090,8 +1090,9 @@ __device__ void setup_query(MidSmem& sm, const PlanDev* __restrict__ P, int q) {
         atomicOr(&sm.bm[bv >> 5], 1u << (bv & 31u));
     }
     __syncthreads();
-    {
-        // rank[b] = set bits in words [0, 8b)
+    if (sigma == 0) {
+        // exact bitmap: rank[b] = set bits in words [0, 8b), so a far vertex's
+        // rank is its far-list index
         const int nblk = (nbw + kRankWords - 1) / kRankWords;
         const int per = (nblk + blockDim.x - 1) / blockDim.x;  // <= 4
         int mine[4] = {0, 0, 0, 0};
@@ -1116,20 +1117,19 @@ __device__ void setup_query(MidSmem& sm, const PlanDev* __restrict__ P, int q) {
     if (sigma > 0) {
         // coarse bitmap (2^sigma vertices per bit): the far list is sorted by
         // vertex, so the vertices of a set bit are contiguous in it; record,
-        // indexed by the bit's rank, the run's first entry and vertex (written
+        // indexed by the bit itself, the run's first entry and vertex (written
         // by the thread at the run's start) and its last vertex and entry
-        // (written by the thread at its end: the other 8-byte half)
+        // (written by the thread at its end: the other 8-byte half).  Entries
+        // of clear bits are stale but never read: the scan reads an entry only
+        // after finding its bit set.
         uint2* fs = reinterpret_cast<uint2*>(P->far_start + static_cast<int64_t>(blockIdx.x) * P->far_cap);
         const int fc = sm.far_cnt;
         for (int k = threadIdx.x; k < fc; k += blockDim.x) {
             const uint32_t fv = far[k].vertex, bv = fv >> sigma;
             const bool first = k == 0 || (far[k - 1].vertex >> sigma) != bv;
             const bool last = k == fc - 1 || (far[k + 1].vertex >> sigma) != bv;
-            if (first || last) {
-                const uint32_t r = bm_rank(sm, bv);
-                if (first) fs[2 * r] = make_uint2(static_cast<uint32_t>(k), fv);
-                if (last) fs[2 * r + 1] = make_uint2(fv, static_cast<uint32_t>(k));
-            }
+            if (first) fs[2 * static_cast<int64_t>(bv)] = make_uint2(static_cast<uint32_t>(k), fv);
+            if (last) fs[2 * static_cast<int64_t>(bv) + 1] = make_uint2(fv, static_cast<uint32_t>(k));
         }
         __syncthreads();
     }
@@ -1793,13 +1793,14 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                     const uint32_t bv = x >> sigma;
                     if ((sm.bm[bv >> 5] >> (bv & 31u)) & 1u) {
                         hit[u] = true;
-                        // exact bitmap: the rank of x is its far-list index
-                        fk[u] = bm_rank(sm, sigma == 0 ? x : bv);
+                        // exact bitmap: the rank of x is its far-list index;
+                        // coarse: the bit indexes the run table
+                        fk[u] = sigma == 0 ? bm_rank(sm, x) : bv;
                     }
                 }
             }
             if (sigma > 0) {
-                // coarse bitmap: far_start[rank] (written by this CTA's query set-up:
+                // coarse bitmap: far_start[bit] (written by this CTA's query set-up:
                 // a coherent load) holds the set bit's run in the far list: first
                 // entry and vertex, last vertex and entry.  x equal to either end is
                 // a hit, x outside them a miss; only x strictly inside a run of three
@@ -2755,8 +2756,8 @@ static mhr_status ensure_slots(Plan* p, int64_t X) {
 // The sequence is captured as three graphs (before, the join, after) so that
 // timing events recorded between their launches on the caller's stream bracket
 // the join kernel exactly.
-// run starts of the coarse far bitmap, one array of `cap` per join CTA (only
-// graphs too large for the exact shared-memory bitmap need them)
+// run table of the coarse far bitmap, one entry per coarse bit and join CTA
+// (only graphs too large for the exact shared-memory bitmap need it)
 static mhr_status ensure_far(Plan* p, int64_t cap) {
     if (p->h.sigma == 0) return MHR_OK;
     cap = std::max<int64_t>(cap, 1);
@@ -3087,10 +3088,8 @@ static mhr_status run_batch(mhr_graph* G, int nq, const uint32_t* hS, const uint
         icap += (bound + chunk - 1) / chunk;
     }
     MHR_TRY(ensure_items(p, icap));
-    // a far list is at most the row of s or the reverse row of t
-    int64_t fcap = 0;
-    for (int q = 0; q < nq; ++q) fcap = std::max(fcap, std::max(pa[q + 1] - pa[q], pc[q + 1] - pc[q]));
-    MHR_TRY(ensure_far(p, fcap));
+    // the coarse bitmap's run table has one entry per bit
+    MHR_TRY(ensure_far(p, static_cast<int64_t>(p->h.nbw) * 32));
     p->h.X = ta + tc;
     p->h.totA = ta;
     p->h.prune = (opts && opts->prune) ? 1 : 0;

@@ -148,9 +148,9 @@ struct PlanDev {
     unsigned long long* counters;  // kCntCount
     unsigned long long* cursors;   // [grid] next item of each CTA's own range
     uint32_t* drained;             // [(grid + 31) / 32] bit v: range v has no item left
-    uint4* far_start;              // [grid x far_cap] coarse bitmap, per set bit's run in the far list:
-                                   // (first entry, its vertex, last vertex, its entry)
-    int64_t far_cap;               // longest far list of the batch (coarse bitmaps only)
+    uint4* far_start;              // [grid x far_cap] coarse bitmap, indexed by the bit: its run in the far
+                                   // list (first entry, its vertex, last vertex, its entry); set bits only
+    int64_t far_cap;               // entries per CTA: the coarse bitmap's bits (coarse bitmaps only)
     int64_t* partials;             // scan scratch
 };
 
