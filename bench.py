@@ -95,7 +95,10 @@ KERNELS_PER_STEP = 22
 # DRAM bytes (read + write) of one main join launch from one ncu capture of the
 # current kernel, per (workload, form, work-item size, scan tile); any other
 # configuration reports null.
-TRAFFIC_NCU = {}  # filled from a capture of the current kernel only
+TRAFFIC_NCU = {# batching workload: the main join launch of the first timed step, one
+               # capture of the current kernel (1 pass: dram__bytes_read.sum +
+               # dram__bytes_write.sum at full size, --profile-range)
+               ("batching", "chosen", 32768, 4): 143_070_000_000}
 
 
 def dist_env():
