@@ -17,8 +17,9 @@
 //   join     a seed launch does the first rows of every multi-item query, then
 //            one persistent 1024-thread CTA per SM takes items from its own
 //            range and steals from the others; the far frontier sits in a
-//            shared-memory bitmap (with a popcount rank, so the join needs no
-//            hash probe), the near rows are streamed warp-cooperatively, every
+//            shared-memory bitmap (with a popcount rank for an exact bitmap,
+//            a run table indexed by the bit for a coarse one, so the join needs
+//            no hash probe), the near rows are streamed warp-cooperatively, every
 //            hit whose bound can reach the kept band is scored in fp32 and
 //            every path whose fp32 score can still reach the top K (within the
 //            proven fp32 error bound of the running K-th score) is kept in a
@@ -1778,10 +1779,10 @@ __global__ void __launch_bounds__(kMidThreads, 1) k_middle(const PlanDev* __rest
                 }
             // Membership of the UNROLL groups' far vertices, in passes whose
             // loads do not depend on one another across groups, so a warp has
-            // all of them in flight at once: bitmap bit and rank (shared
-            // memory), then for a coarse bitmap the start of the set bit's run
-            // in the far list and the first far vertex of that run (global),
-            // then the rare walk along the run.
+            // all of them in flight at once: bitmap bit (and, for an exact
+            // bitmap, its rank: the far-list index) in shared memory, then for a
+            // coarse bitmap the set bit's run in the far list from the run
+            // table (global), then the rare walk along the run.
             bool hit[UNROLL];
             uint32_t fk[UNROLL];
 #pragma unroll
